@@ -1,0 +1,371 @@
+"""Benchmark: viewport-dependent decoding of 8192x8192 wavelet video on GB300.
+
+Workload (one step): an 8-frame group of 8192x8192 equirectangular YCbCr 4:2:0
+frames (seeded band-limited noise + 50 textured discs moving 2 px/frame),
+5-level CDF 9/7, 1-level inter-frame Haar over pairs, dead-zone step 4,
+256x256 coefficient blocks; 64 seeded head poses (yaw U[-pi, pi), pitch
+U[-pi/4, pi/4]), 110 degree field of view, 2160x2160 RGBA output, pose i
+decoding frame i mod 8.  A step decodes the 64 viewports with
+wv_decode_viewport (footprint, tile selection, fused tile decode, resample).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (plain
+fp64 decoder) on bounded samples of the same workload instead.
+
+Multi-GPU: viewports are independent (replicas only): every rank decodes the
+same workload on its own GPU with no collective on the data path; the value is
+the viewports of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "viewport frames/s at 8192^2 (9/7)"
+UNIT = "viewports/s"
+SIZE, FRAMES, LEVELS, STEP, BLOCK, TLEVELS = 8192, 8, 5, 4.0, 256, 1
+OUT, FOV_DEG, POSES = 2160, 110.0, 64
+WORKLOAD = ("8192x8192 equirect YCbCr 4:2:0, 8-frame group, 5-level CDF 9/7 float32, "
+            "1-level inter-frame Haar, dead-zone step 4, 256x256 blocks; 64 poses, "
+            "110 deg FOV, 2160x2160 RGBA per viewport")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-poses", type=int, default=2,
+                    help="viewports the oracle decodes for the CPU baseline")
+    ap.add_argument("--size", type=int, default=SIZE, help=argparse.SUPPRESS)
+    ap.add_argument("--poses", type=int, default=POSES, help=argparse.SUPPRESS)
+    ap.add_argument("--out", type=int, default=OUT, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload(size):
+    import synth
+    frames = synth.equirect_gop(size, FRAMES, seed=2, n_discs=50)
+    poses = synth.random_poses(POSES, seed=3)
+    return frames, poses
+
+
+def desc(size):
+    return dict(width=size, height=size, planes=3, chroma_420=1, levels=LEVELS, wavelet=1,
+                num_frames=FRAMES, tlevels=TLEVELS, block=BLOCK, quant=0, step=STEP)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = max(smax, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """dram bytes per decode_tiles launch from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "decode_tiles_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_2208_10859_gb300", "csrc", "ifwt.cu"), "rb").read()
+    if rec.get("ifwt_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    return rec
+
+
+def cpu_baseline_leg(frames, poses, size, n_poses):
+    """Time the oracle as it stands (single-threaded plain decoder: whole
+    frame, then reprojection) on n_poses viewports.  The oracle decodes a
+    stream its own encoder made from the first inter-frame set."""
+    import oracle as O
+    p = O.Params(size, size, 3, 1, LEVELS, O.WAVELET_97, 2, TLEVELS, BLOCK, STEP)
+    st = O.Stream(O.encode(frames[:2], p))
+    fov = math.radians(FOV_DEG)
+    t0 = time.perf_counter()
+    for i in range(n_poses):
+        yaw, pitch = poses[i]
+        O.viewport(st, i % 2, yaw, pitch, fov, OUT, OUT)
+    dt = time.perf_counter() - t0
+    return {"value": n_poses / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_poses} viewports of the same workload (frames 0-1, poses 0..{n_poses - 1}), "
+                      f"{dt:.1f} s single-threaded fp64 decode of the whole frame then reprojection"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    frames, poses = workload(args.size)
+    import oracle as O
+    p = O.Params(args.size, args.size, 3, 1, LEVELS, O.WAVELET_97, 2, TLEVELS, BLOCK, STEP)
+    st = O.Stream(O.encode(frames[:2], p))
+    fov = math.radians(FOV_DEG)
+    times = []
+    for k in range(args.warmup + args.steps):
+        yaw, pitch = poses[k % len(poses)]
+        t0 = time.perf_counter()
+        O.viewport(st, k % 2, yaw, pitch, fov, OUT, OUT)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = len(times) / sum(times)
+    sample = f"each step one viewport of the workload (frames 0-1), single-threaded fp64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2208_10859_gb300 import wv
+    import __graft_entry__
+    __graft_entry__.build()
+
+    size = args.size
+    frames, poses = workload(size)
+    poses = poses[:args.poses]
+    fov = math.radians(FOV_DEG)
+    dframes = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in frames]
+    data = wv.encode(dframes, desc(size))
+    del dframes
+    torch.cuda.empty_cache()
+    stream = torch.cuda.Stream(device=dev)
+    s = wv.Stream(data, cuda_stream=stream)
+    outs = [torch.empty((args.out, args.out, 4), dtype=torch.uint8, device=dev) for _ in poses]
+
+    def step():
+        for i, (yaw, pitch) in enumerate(poses):
+            s.decode_viewport(i % FRAMES, yaw, pitch, fov, outs[i])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # algorithmic bytes per pose: exact coefficient cone + decoded samples + RGBA
+    cone, region = [], []
+    for i, (yaw, pitch) in enumerate(poses):
+        mask, _ = s.debug_footprint(yaw, pitch, fov, args.out, args.out)
+        cone.append(s.cone_bytes(i % FRAMES, mask))
+        region.append(int(mask.sum()) * 32 * 32 * 3 // 2)
+    out_bytes = args.out * args.out * 4
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_view = args.steps * len(poses) * world
+    value = n_view / (ms / 1e3)
+    if s.sync_status() != 0:
+        raise RuntimeError("device error during the timed region")
+
+    # per-kernel device time (events on the decode stream, separate pass)
+    s.profile_begin()
+    for _ in range(args.steps):
+        step()
+    prof = s.profile_end()
+    dec_ms, dec_n = prof["decode_tiles"]
+    alg_dec = sum(cone) + sum(region)   # per pass over the poses
+    achieved = alg_dec * args.steps / (dec_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    trec = traffic_record()
+    kernel_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if k != "tiles"}
+
+    # end to end through the C ABI with host buffers: upload the coded group
+    # from pinned memory (open), decode the 64 viewports, read them back
+    pinned_in = torch.from_numpy(np.frombuffer(data, np.uint8)).pin_memory()
+    host_out = [torch.empty((args.out, args.out, 4), dtype=torch.uint8).pin_memory() for _ in poses]
+    import ctypes
+
+    def e2e_step():
+        desc_, need = wv.query(data)
+        mem = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        base = (mem.data_ptr() + 255) & ~255
+        h = ctypes.c_void_p()
+        rc = wv._lib().wv_open_stream(ctypes.c_void_p(pinned_in.data_ptr()), len(data), ctypes.c_void_p(base),
+                                      need, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"wv_open_stream {rc}")
+        for i, (yaw, pitch) in enumerate(poses):
+            img = wv.Image(outs[i].data_ptr(), args.out, args.out, args.out * 4)
+            rc = wv._lib().wv_decode_viewport(h, i % FRAMES, yaw, pitch, fov, ctypes.byref(img))
+            if rc != 0:
+                raise RuntimeError(f"wv_decode_viewport {rc}")
+            with torch.cuda.stream(stream):
+                host_out[i].copy_(outs[i], non_blocking=True)
+        wv._lib().wv_close_stream(h)
+        return mem
+
+    e2e_steps = max(2, args.steps // 4)
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    te0 = time.perf_counter()
+    keep = None
+    for _ in range(e2e_steps):
+        keep = e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - te0
+    del keep
+    e2e_value = e2e_steps * len(poses) * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_leg(frames, poses, size, args.cpu_poses)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "poses_per_step": len(poses),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"inputs larger than L2: coded group {len(data) / 1e9:.2f} GB device-resident",
+                       "stream_bytes": len(data)},
+            "gpu_launches": args.steps * len(poses) * wv.launches_per_viewport(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(data),
+                    "d2h_bytes_per_step": len(poses) * out_bytes,
+                    "note": "per step: wv_open_stream from pinned host bytes, 64 wv_decode_viewport, "
+                            "64 RGBA reads to pinned host memory"},
+            "roofline": {"kernel": "decode_tiles", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None if trec is None else trec["traffic_bytes_per_launch"],
+                         "algorithmic_bytes_per_launch": alg_dec / len(poses),
+                         "avg_launch_ms": dec_ms / max(1, dec_n)},
+            "kernel_ms_per_launch": kernel_ms,
+            "viewport_bytes": {"cone_coef_mean": sum(cone) / len(cone), "region_mean": sum(region) / len(region),
+                               "rgba": out_bytes,
+                               "whole_path_alg_GBps": (sum(cone) + len(poses) * out_bytes) * args.steps / (ms / 1e3) / 1e9},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

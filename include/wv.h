@@ -1,0 +1,242 @@
+/*
+ * wv.h -- C ABI of the GB300 viewport-dependent wavelet video decoder.
+ *
+ * The method is the wavelet-based 360-degree video codec of Groth, Fricke,
+ * Castillo and Magnor, "Wavelet-Based Fast Decoding of 360 deg Videos":
+ *   - frame-wise 2D fast wavelet transform, CDF 9/7 (Sec. 3.1) or the
+ *     reversible LeGall 5/3 integer wavelet (Sec. 2.2);
+ *   - inter-frame Haar transform along time over sets of 2^k frames, run to
+ *     the last level, applied to the 2D coefficients (Sec. 3.2);
+ *   - quantised coefficients stored in blocks with a per-block table
+ *     (the BlockEnd pointers of Sec. 3.4);
+ *   - decoding of only the viewport of the current frame for the current head
+ *     pose: a low-resolution binary mask marks the region to reconstruct
+ *     (Sec. 3.1), the inverse inter-frame transform runs over the needed
+ *     coefficients (Sec. 3.2, 3.5), the masked 2D iFWT follows (Sec. 3.5) and
+ *     a mapping pass reprojects the equirectangular result into the viewport
+ *     (Sec. 3.6).
+ *
+ * Conventions for every call:
+ *   - Return value: WV_OK (0) or a negative WV_ERR_* code; wv_strerror() names
+ *     it.  Nothing is printed and nothing aborts.
+ *   - Device pointers are CUDA global-memory addresses of the current device;
+ *     host pointers are ordinary process memory.  The library never frees
+ *     memory it did not allocate.
+ *   - Decode calls are asynchronous: they enqueue kernels on the stream's CUDA
+ *     stream (set at open, changed by wv_set_cuda_stream) and return before
+ *     the GPU finishes; outputs are valid once that CUDA stream is
+ *     synchronised.  Device-side errors are reported by wv_stream_sync_status.
+ *   - A wv_stream may be used by one host thread at a time.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns WV_ERR_CUDA.
+ *   - Angles are radians.  Yaw turns about +y (from +z toward +x), pitch about
+ *     +x (positive looks up), no roll.  `fov` is the full field of view,
+ *     horizontal and vertical (square pixels in the viewport).
+ */
+#ifndef WV_H
+#define WV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WV_OK 0
+#define WV_ERR_ARG (-1)      /* invalid argument (NULL, range, size)           */
+#define WV_ERR_FORMAT (-2)   /* malformed or unsupported stream bytes          */
+#define WV_ERR_OOM (-3)      /* caller-provided memory too small / alloc fail  */
+#define WV_ERR_CUDA (-4)     /* CUDA runtime error or no device                */
+#define WV_ERR_RANGE (-5)    /* value out of representable range (encoder)     */
+#define WV_ERR_TIMEOUT (-6)  /* a bounded device-side wait gave up             */
+#define WV_ERR_DEVICE (-7)   /* a kernel reported an inconsistency (err word)  */
+
+#define WV_WAVELET_53 0      /* LeGall 5/3, reversible integer lifting         */
+#define WV_WAVELET_97 1      /* CDF 9/7, float lifting                          */
+
+/* Geometry and coding parameters of a stream (the header of Sec. 3.4: number
+ * of frames, frame size, number of wavelet levels; plus the fields this
+ * format adds).  width/height are luma sizes; with chroma_420 the Cb and Cr
+ * planes are half width and half height.  Every plane side must be divisible
+ * by 2^levels.  The inter-frame set holds 2^tlevels frames (Sec. 3.2);
+ * num_frames is a multiple of it.  block is the side of the square
+ * coefficient blocks (a power of two, 16..256).  quant 0 = dead-zone uniform
+ * quantiser with step `step` (integer >= 1 for 5/3). */
+typedef struct {
+    int width, height;
+    int planes;        /* 1 (grey) or 3 (Y, Cb, Cr) */
+    int chroma_420;    /* 1: Cb/Cr subsampled 2x2, centre-sited */
+    int levels;        /* spatial wavelet levels, 1..6 */
+    int wavelet;       /* WV_WAVELET_53 or WV_WAVELET_97 */
+    int num_frames;
+    int tlevels;       /* inter-frame Haar levels k, 0..3 */
+    int block;
+    int quant;
+    float step;
+} wv_stream_desc;
+
+/* An RGBA8 output image in device memory, owned by the caller.  Row r starts
+ * at dptr + r * pitch_bytes; pitch_bytes >= 4 * width. */
+typedef struct {
+    void *dptr;
+    int width, height;
+    size_t pitch_bytes;
+} wv_image;
+
+typedef struct wv_stream wv_stream;
+
+/* ---------------------------------------------------------------------------
+ * Stream lifetime
+ * ------------------------------------------------------------------------- */
+
+/* Parse the stream header and block table in `bytes` (n bytes, host memory)
+ * and validate them (Sec. 3.4: header and metadata are preloaded).  Fills
+ * *desc if desc != NULL and the number of device bytes wv_open_stream needs
+ * in *device_bytes if device_bytes != NULL.  Returns WV_ERR_FORMAT for a
+ * truncated or inconsistent stream. */
+int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc,
+                    size_t *device_bytes);
+
+/* Open a stream: validate the bytes, copy the block table and the coefficient
+ * payload to the device and set up per-stream decode scratch (reconstruction
+ * planes, mask, tile list).  device_mem is a device buffer of at least
+ * device_bytes (from wv_stream_query) that the caller owns and keeps alive
+ * until wv_close_stream; pass NULL to let the library allocate (and later
+ * free) it.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * The host bytes may be freed once this call returns.  On success *out holds
+ * the new stream. */
+int wv_open_stream(const void *bytes, size_t n, void *device_mem,
+                   size_t device_bytes, void *cuda_stream, wv_stream **out);
+
+/* Use another CUDA stream for the following calls on s. */
+int wv_set_cuda_stream(wv_stream *s, void *cuda_stream);
+
+/* Release the stream object (and its device memory if the library allocated
+ * it).  Waits for work already enqueued on the stream's CUDA stream. */
+void wv_close_stream(wv_stream *s);
+
+/* Describe an error code (static string). */
+const char *wv_strerror(int code);
+
+/* ---------------------------------------------------------------------------
+ * Decoding
+ * ------------------------------------------------------------------------- */
+
+/* Decode the viewport of frame `frame` seen from head pose (yaw, pitch) with
+ * field of view fov into out (RGBA8, out->width x out->height, device).
+ * Steps (all on the GPU, enqueued on the stream's CUDA stream):
+ *   1. footprint: every viewport pixel is projected onto the equirectangular
+ *      frame and the 32-pixel cells its bilinear taps touch are marked (the
+ *      low-resolution binary mask of Sec. 3.1);
+ *   2. the mask becomes a list of output tiles;
+ *   3. per tile, the needed coefficients of every level are gathered,
+ *      dequantised and rebuilt along time (inverse inter-frame Haar, Sec.
+ *      3.2/3.5) and all levels of the 2D iFWT run in one pass (Sec. 3.1);
+ *   4. the decoded region is reprojected into the viewport with bilinear
+ *      filtering and converted from YCbCr (BT.709, full range) to RGBA
+ *      (Sec. 3.6).
+ * Grey streams give R = G = B = Y.  Returns WV_ERR_ARG for a frame outside
+ * [0, num_frames), fov outside (0, pi) or a bad image. */
+int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch,
+                       float fov, const wv_image *out);
+
+/* One viewport request of a batch. */
+typedef struct {
+    wv_stream *s;
+    int frame;
+    float yaw, pitch, fov;
+    wv_image out;
+} wv_request;
+
+/* Decode n viewport requests, possibly of different streams, enqueued on
+ * cuda_stream (NULL = legacy default stream).  Each result equals the
+ * result of wv_decode_viewport for the same request.  Requests sharing a
+ * wv_stream are decoded one after the other. */
+int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream);
+
+/* Decode a whole plane of one frame (all tiles) -- the full-frame case, used
+ * for the lossless workload and for parity checks.  dptr receives width x
+ * height samples of the plane, row-major and tightly packed: uint8
+ * (as_float = 0) or float32 values before rounding (as_float = 1, 8-bit
+ * units, DC offset included).  dptr == NULL decodes into the stream's own
+ * reconstruction plane (as uint8) for wv_resample_at. */
+int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float);
+
+/* Wait for the stream's CUDA stream and read the device error word: WV_OK,
+ * or the first error a kernel recorded since the previous call (the word is
+ * then cleared). */
+int wv_stream_sync_status(wv_stream *s);
+
+/* ---------------------------------------------------------------------------
+ * Inspection and measurement (tests, benchmark)
+ * ------------------------------------------------------------------------- */
+
+/* Footprint of a viewport: runs step 1 of wv_decode_viewport and copies the
+ * cell mask (height/32 rows x width/32 columns of 0/1 bytes) to mask_host
+ * (host memory) and the number of tiles step 2 selects to *tiles.
+ * Synchronises the stream's CUDA stream. */
+int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov,
+                       int out_w, int out_h, uint8_t *mask_host, int *tiles);
+
+/* Equirectangular positions (u, v) that the viewport's pixels sample, as
+ * computed on the device (float32 pairs, out_h x out_w x 2, device memory). */
+int wv_debug_project(wv_stream *s, float yaw, float pitch, float fov,
+                     int out_w, int out_h, float *uv_dev);
+
+/* Resample and colour-convert the stream's reconstruction planes (filled by
+ * wv_decode_full with dptr == NULL) at caller-given luma positions uv_dev
+ * (device float32 pairs, out->height x out->width x 2) into out. */
+int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out);
+
+/* Bytes of quantised coefficients the masked iFWT of frame `frame` needs for
+ * the cell mask mask_host (height/32 x width/32 bytes, host): the exact
+ * dependency cone of the marked pixels through every level (synthesis
+ * filter supports, symmetric extension), restricted to stored blocks,
+ * 2 bytes per coefficient, summed over the coefficient frames the
+ * inter-frame rebuild reads.  Host computation. */
+int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
+                  unsigned long long *bytes);
+
+/* Per-kernel device time of the calls since the last wv_profile_begin,
+ * measured with CUDA events recorded on the stream's CUDA stream around
+ * each launch. */
+typedef struct {
+    double ms[8];        /* footprint, tiles, decode tiles, resample, ... */
+    int launches[8];
+    int tiles;           /* tiles decoded by the last viewport */
+} wv_profile;
+
+int wv_profile_begin(wv_stream *s);
+/* Synchronises, sums the recorded event intervals into *out and stops. */
+int wv_profile_end(wv_stream *s, wv_profile *out);
+
+/* Number of kernel launches a wv_decode_viewport call makes. */
+int wv_launches_per_viewport(void);
+
+/* ---------------------------------------------------------------------------
+ * Encoder (offline; not part of the decode path)
+ * ------------------------------------------------------------------------- */
+
+/* Device scratch (bytes) and the largest stream (bytes) wv_encode may need
+ * for frames of this description. */
+int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes,
+                    size_t *max_stream_bytes);
+
+/* Encode desc->num_frames frames on the GPU: DC shift and 2D FWT per frame
+ * and plane (Sec. 3.1, float32 for 9/7 as in Sec. 3.3, int32 for 5/3),
+ * inter-frame Haar per set (Sec. 3.2), dead-zone quantisation, blocking with
+ * all-zero blocks omitted (Sec. 3.4).  planes_dev holds num_frames * planes
+ * device pointers to tightly packed uint8 planes (frame-major).  The stream
+ * is written to host memory out (capacity cap); *out_len receives its
+ * length.  Returns WV_ERR_OOM if cap or scratch_bytes is too small and
+ * WV_ERR_RANGE if a quantised coefficient does not fit in int16.
+ * Synchronises cuda_stream. */
+int wv_encode(const wv_stream_desc *desc, const void *const *planes_dev,
+              void *scratch_dev, size_t scratch_bytes, void *out, size_t cap,
+              size_t *out_len, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WV_H */

@@ -1,0 +1,578 @@
+// api.cu -- C ABI of the decoder: stream parsing and upload, decode
+// orchestration, inspection hooks and per-kernel event timing.
+//
+// Stream layout (little endian):
+//   header (128 bytes)  magic "WVS1", version 1, luma width/height, planes,
+//                       chroma_420, levels, wavelet, num_frames, tlevels,
+//                       block, quantiser, step, blocks per frame, number of
+//                       stored blocks, byte offsets of table and payload.
+//                       (Sec. 3.4: the header gives the number of frames, the
+//                       frame size and the number of wavelet levels.)
+//   block table         int32 [num_frames][blocks per frame]: slot of the
+//                       block's coefficients in the payload, -1 when the block
+//                       is all zero (the per-block BlockEnd pointers of Sec.
+//                       3.4, here one fixed-size slot per stored block).
+//   payload             int16 [slots][block][block], row-major blocks.
+// Blocks of one coefficient frame: plane by plane; in each plane LL_L, then
+// for l = L..1 the subbands HL_l, LH_l, HH_l (level-wise from the lowest
+// frequency, Sec. 3.4), each cut into block x block tiles in row-major order.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "wv_impl.h"
+
+using namespace wv;
+
+namespace {
+
+enum Kernel { kKFootprint = 0, kKTiles = 1, kKDecode = 2, kKResample = 3 };
+constexpr int kLaunchesPerViewport = 4;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
+    if (!bytes || n < kHeaderBytes) return WV_ERR_FORMAT;
+    memcpy(h, bytes, sizeof(StreamHeader));
+    if (memcmp(h->magic, "WVS1", 4) != 0 || h->version != 1) return WV_ERR_FORMAT;
+    d->width = (int)h->width;
+    d->height = (int)h->height;
+    d->planes = (int)h->planes;
+    d->chroma_420 = (int)h->c420;
+    d->levels = (int)h->levels;
+    d->wavelet = (int)h->wavelet;
+    d->num_frames = (int)h->num_frames;
+    d->tlevels = (int)h->tlevels;
+    d->block = (int)h->block;
+    d->quant = (int)h->quant;
+    d->step = h->step;
+    Geom g;
+    if (build_geom(*d, &g) != WV_OK) return WV_ERR_FORMAT;
+    if ((int)h->nbpf != g.nbpf) return WV_ERR_FORMAT;
+    const uint64_t tbytes = (uint64_t)g.num_frames * g.nbpf * 4;
+    const uint64_t bsz = (uint64_t)g.block * g.block * 2;
+    if (h->table_off < kHeaderBytes || h->table_off + tbytes > n) return WV_ERR_FORMAT;
+    if (h->payload_off % 2 || h->payload_off < h->table_off + tbytes) return WV_ERR_FORMAT;
+    if (h->n_payload > (n - std::min<uint64_t>(n, h->payload_off)) / bsz) return WV_ERR_FORMAT;
+    const int32_t *tab = reinterpret_cast<const int32_t *>((const char *)bytes + h->table_off);
+    for (uint64_t i = 0; i < (uint64_t)g.num_frames * g.nbpf; ++i) {
+        int32_t s;
+        memcpy(&s, tab + i, 4);
+        if (s < -1 || (int64_t)s >= (int64_t)h->n_payload) return WV_ERR_FORMAT;
+    }
+    return WV_OK;
+}
+
+struct Layout {
+    size_t payload, table, recon[3], mask[2], tiles, counters, err, total;
+};
+
+Layout layout(const Geom &g, uint64_t n_payload) {
+    Layout L;
+    size_t o = 0;
+    L.payload = o;
+    o = align256(o + n_payload * g.block * g.block * 2);
+    L.table = o;
+    o = align256(o + (size_t)g.num_frames * g.nbpf * 4);
+    for (int p = 0; p < 3; ++p) {
+        L.recon[p] = o;
+        if (p < g.planes) o = align256(o + (size_t)g.p[p].w * g.p[p].h);
+    }
+    for (int m = 0; m < 2; ++m) {
+        L.mask[m] = o;
+        o = align256(o + (size_t)g.cells_x * g.cells_y);
+    }
+    L.tiles = o;
+    o = align256(o + (size_t)g.total_tiles * 4);
+    L.counters = o;
+    o = align256(o + 64);
+    L.err = o;
+    o = align256(o + 64);
+    L.total = o;
+    return L;
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? WV_OK : WV_ERR_CUDA; }
+
+void prof_begin(wv_stream *s, int kind) {
+    if (!s->prof) return;
+    if (s->ev_used + 2 > s->ev_pool.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            s->ev_pool.push_back(e);
+        }
+    }
+    cudaEventRecord(s->ev_pool[s->ev_used], s->cs);
+    s->ev_kind.push_back(kind);
+}
+
+void prof_end(wv_stream *s) {
+    if (!s->prof) return;
+    cudaEventRecord(s->ev_pool[s->ev_used + 1], s->cs);
+    s->ev_used += 2;
+}
+
+int check_image(const wv_image *o) {
+    if (!o || !o->dptr || o->width <= 0 || o->height <= 0 ||
+        o->pitch_bytes < (size_t)o->width * 4 || (o->pitch_bytes % 4) != 0 ||
+        ((uintptr_t)o->dptr % 4) != 0)
+        return WV_ERR_ARG;
+    return WV_OK;
+}
+
+int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
+                    const wv_image *out) {
+    if (!s) return WV_ERR_ARG;
+    if (frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
+    if (!(fov > 0.f && fov < 3.14159f) || !isfinite(yaw) || !isfinite(pitch)) return WV_ERR_ARG;
+    if (check_image(out) != WV_OK) return WV_ERR_ARG;
+    const Geom &g = s->g;
+    const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, g.p[0].h);
+    const Bands b = frame_bands(g, frame);
+    uint8_t *m = s->mask[s->mask_parity];
+    uint8_t *other = s->mask[s->mask_parity ^ 1];
+    prof_begin(s, kKFootprint);
+    launch_footprint(g, v, m, s->counters, s->cs);
+    prof_end(s);
+    prof_begin(s, kKTiles);
+    launch_select_tiles(g, m, other, s->tiles, s->counters, s->cs);
+    prof_end(s);
+    s->mask_parity ^= 1;
+    prof_begin(s, kKDecode);
+    cudaError_t e = launch_decode_tiles(g, s->payload, s->table, b, s->recon, nullptr, -1,
+                                        s->tiles, s->counters, s->err, s->cs);
+    prof_end(s);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    prof_begin(s, kKResample);
+    launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
+    prof_end(s);
+    return cuda_err(cudaGetLastError());
+}
+
+// ---- host-side dependency cone (accounting only) ----
+
+void dilate_axis(const std::vector<uint8_t> &in, std::vector<uint8_t> &out, int w, int h,
+                 bool along_x, int wavelet) {
+    out.assign(in.size(), 0);
+    const int n = along_x ? w : h;
+    auto refl = [n](int i) {
+        if (n == 1) return 0;
+        const int period = 2 * (n - 1);
+        i %= period;
+        if (i < 0) i += period;
+        return i >= n ? period - i : i;
+    };
+    // synthesis output i reads interleaved inputs i-3..i+3 (even i) or i-4..i+4
+    // (odd i) for 9/7, i-1..i+1 or i-2..i+2 for 5/3
+    const int se = wavelet == WV_WAVELET_97 ? 3 : 1;
+    const int so = wavelet == WV_WAVELET_97 ? 4 : 2;
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            if (!in[(size_t)y * w + x]) continue;
+            const int i = along_x ? x : y;
+            const int r = (i & 1) ? so : se;
+            for (int o = -r; o <= r; ++o) {
+                const int j = refl(i + o);
+                if (along_x) out[(size_t)y * w + j] = 1;
+                else out[(size_t)j * w + x] = 1;
+            }
+        }
+    }
+}
+
+unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask) {
+    const Geom &g = s->g;
+    const Bands b = frame_bands(g, frame);
+    unsigned long long total = 0;
+    for (int p = 0; p < g.planes; ++p) {
+        const PlaneGeom &pg = g.p[p];
+        int w = pg.w, h = pg.h;
+        const int cell = kCell / pg.sub;
+        std::vector<uint8_t> R((size_t)w * h), X, tmp;
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x)
+                R[(size_t)y * w + x] = mask[(size_t)(y / cell) * g.cells_x + x / cell] ? 1 : 0;
+        auto count = [&](int level, int sub, int kx, int ky) {
+            const int bid = pg.base[level][sub] + (ky >> g.log2b) * pg.nbx[level] + (kx >> g.log2b);
+            for (int k = 0; k < b.n; ++k)
+                if (s->table_host[(size_t)b.t[k] * g.nbpf + bid] >= 0) total += 2;
+        };
+        for (int l = 1; l <= g.levels; ++l) {
+            dilate_axis(R, tmp, w, h, true, g.wavelet);
+            dilate_axis(tmp, X, w, h, false, g.wavelet);
+            std::vector<uint8_t> next((size_t)(w / 2) * (h / 2));
+            for (int y = 0; y < h; ++y)
+                for (int x = 0; x < w; ++x) {
+                    if (!X[(size_t)y * w + x]) continue;
+                    const int sub = (x & 1) + 2 * (y & 1);
+                    if (sub == 0) next[(size_t)(y >> 1) * (w / 2) + (x >> 1)] = 1;
+                    else count(l, sub, x >> 1, y >> 1);
+                }
+            R.swap(next);
+            w /= 2;
+            h /= 2;
+        }
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x)
+                if (R[(size_t)y * w + x]) count(g.levels, 0, x, y);
+    }
+    return total;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// geometry helpers
+// ---------------------------------------------------------------------------
+
+namespace wv {
+
+int build_geom(const wv_stream_desc &d, Geom *g) {
+    memset(g, 0, sizeof(*g));
+    if (d.planes != 1 && d.planes != 3) return WV_ERR_ARG;
+    if (d.chroma_420 != 0 && d.chroma_420 != 1) return WV_ERR_ARG;
+    if (d.levels < 1 || d.levels > kMaxLevels) return WV_ERR_ARG;
+    if (d.wavelet != WV_WAVELET_53 && d.wavelet != WV_WAVELET_97) return WV_ERR_ARG;
+    if (d.tlevels < 0 || d.tlevels > kMaxBands - 1) return WV_ERR_ARG;
+    if (d.num_frames < 1 || d.num_frames % (1 << d.tlevels)) return WV_ERR_ARG;
+    if (d.block < 16 || d.block > 256 || (d.block & (d.block - 1))) return WV_ERR_ARG;
+    if (d.quant != 0 || !(d.step > 0.f) || !isfinite(d.step)) return WV_ERR_ARG;
+    if (d.wavelet == WV_WAVELET_53 && (d.step != floorf(d.step) || d.step > 65536.f))
+        return WV_ERR_ARG;
+    if (d.width < 2 || d.height < 2 || d.width > 16384 || d.height > 16384) return WV_ERR_ARG;
+    if (d.width % kCell || d.height % kCell) return WV_ERR_ARG;
+    g->planes = d.planes;
+    g->c420 = d.planes == 3 ? d.chroma_420 : 0;
+    g->levels = d.levels;
+    g->wavelet = d.wavelet;
+    g->num_frames = d.num_frames;
+    g->tlevels = d.tlevels;
+    g->block = d.block;
+    g->log2b = 0;
+    while ((1 << g->log2b) < d.block) ++g->log2b;
+    g->step = d.step;
+    g->cells_x = d.width / kCell;
+    g->cells_y = d.height / kCell;
+    int id = 0;
+    g->total_tiles = 0;
+    for (int p = 0; p < d.planes; ++p) {
+        PlaneGeom &pg = g->p[p];
+        pg.sub = (p > 0 && g->c420) ? 2 : 1;
+        pg.w = d.width / pg.sub;
+        pg.h = d.height / pg.sub;
+        if (pg.w % (1 << d.levels) || pg.h % (1 << d.levels)) return WV_ERR_ARG;
+        if ((pg.w >> d.levels) < 2 || (pg.h >> d.levels) < 2) return WV_ERR_ARG;
+        for (int l = 1; l <= d.levels; ++l) {
+            const int sw = pg.w >> l, sh = pg.h >> l;
+            pg.nbx[l] = (sw + d.block - 1) / d.block;
+            pg.nby[l] = (sh + d.block - 1) / d.block;
+        }
+        const int L = d.levels;
+        pg.base[L][0] = id;
+        id += pg.nbx[L] * pg.nby[L];
+        for (int l = L; l >= 1; --l)
+            for (int s = 1; s <= 3; ++s) {
+                pg.base[l][s] = id;
+                id += pg.nbx[l] * pg.nby[l];
+            }
+        pg.tiles_x = (pg.w + kTile - 1) / kTile;
+        pg.tiles_y = (pg.h + kTile - 1) / kTile;
+        g->total_tiles += pg.tiles_x * pg.tiles_y;
+    }
+    g->nbpf = id;
+    return WV_OK;
+}
+
+Bands frame_bands(const Geom &g, int frame) {
+    Bands b;
+    const int k = g.tlevels, n = 1 << k;
+    const int set = frame / n, fl = frame % n;
+    b.n = 1 + k;
+    b.t[0] = set * n;
+    b.bit[0] = 0;
+    int idx = 1;
+    for (int j = k; j >= 1; --j, ++idx) {
+        b.t[idx] = set * n + (1 << (k - j)) + (fl >> j);
+        b.bit[idx] = (fl >> (j - 1)) & 1;
+    }
+    for (; idx < kMaxBands; ++idx) {
+        b.t[idx] = 0;
+        b.bit[idx] = 0;
+    }
+    return b;
+}
+
+View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h) {
+    const double cy = cos((double)yaw), sy = sin((double)yaw);
+    const double cp = cos((double)pitch), sp = sin((double)pitch);
+    // R = R_y(yaw) R_x(pitch); R_x: (x, y, z) -> (x, y cp + z sp, -y sp + z cp)
+    const double R[9] = {cy, -sy * sp, sy * cp,
+                         0.0, cp, sp,
+                         -sy, -cy * sp, cy * cp};
+    View v;
+    for (int i = 0; i < 9; ++i) v.r[i] = (float)R[i];
+    v.t = (float)tan((double)fov / 2.0);
+    v.sx = (float)(2.0 / out_w);
+    v.sy = (float)(2.0 / out_h);
+    const double pi = 3.14159265358979323846;
+    v.ku = (float)(eq_w / (2.0 * pi));
+    v.cu = (float)(0.5 * eq_w - 0.5);
+    v.kv = (float)(-eq_h / pi);
+    v.cv = (float)(0.5 * eq_h - 0.5);
+    v.out_w = out_w;
+    v.out_h = out_h;
+    return v;
+}
+
+}  // namespace wv
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *wv_strerror(int code) {
+    switch (code) {
+    case WV_OK: return "ok";
+    case WV_ERR_ARG: return "invalid argument";
+    case WV_ERR_FORMAT: return "malformed or unsupported stream";
+    case WV_ERR_OOM: return "out of memory or buffer too small";
+    case WV_ERR_CUDA: return "CUDA error or no CUDA device";
+    case WV_ERR_RANGE: return "value out of range";
+    case WV_ERR_TIMEOUT: return "device wait timed out";
+    case WV_ERR_DEVICE: return "kernel reported an inconsistency";
+    default: return "unknown error";
+    }
+}
+
+int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc, size_t *device_bytes) {
+    wv_stream_desc d;
+    StreamHeader h;
+    const int rc = parse(bytes, n, &d, &h);
+    if (rc != WV_OK) return rc;
+    if (desc) *desc = d;
+    if (device_bytes) {
+        Geom g;
+        build_geom(d, &g);
+        *device_bytes = layout(g, h.n_payload).total;
+    }
+    return WV_OK;
+}
+
+int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_bytes,
+                   void *cuda_stream, wv_stream **out) {
+    if (!out) return WV_ERR_ARG;
+    *out = nullptr;
+    wv_stream_desc d;
+    StreamHeader h;
+    int rc = parse(bytes, n, &d, &h);
+    if (rc != WV_OK) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return WV_ERR_CUDA;
+    wv_stream *s = new (std::nothrow) wv_stream();
+    if (!s) return WV_ERR_OOM;
+    build_geom(d, &s->g);
+    cudaGetDevice(&s->device);
+    s->cs = (cudaStream_t)cuda_stream;
+    s->n_payload = h.n_payload;
+    const Layout L = layout(s->g, h.n_payload);
+    if (device_mem) {
+        if (device_bytes < L.total || ((uintptr_t)device_mem % 256)) {
+            delete s;
+            return WV_ERR_OOM;
+        }
+        s->dmem = device_mem;
+    } else {
+        if (cudaMalloc(&s->dmem, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return WV_ERR_OOM;
+        }
+        s->owns = true;
+    }
+    s->dbytes = L.total;
+    char *base = (char *)s->dmem;
+    s->payload = (int16_t *)(base + L.payload);
+    s->table = (int32_t *)(base + L.table);
+    for (int p = 0; p < 3; ++p) s->recon[p] = p < s->g.planes ? (uint8_t *)(base + L.recon[p]) : nullptr;
+    s->mask[0] = (uint8_t *)(base + L.mask[0]);
+    s->mask[1] = (uint8_t *)(base + L.mask[1]);
+    s->tiles = (uint32_t *)(base + L.tiles);
+    s->counters = (int *)(base + L.counters);
+    s->err = (int *)(base + L.err);
+    const size_t tcount = (size_t)s->g.num_frames * s->g.nbpf;
+    s->table_host.resize(tcount);
+    memcpy(s->table_host.data(), (const char *)bytes + h.table_off, tcount * 4);
+    cudaError_t e = cudaMemcpyAsync(s->table, s->table_host.data(), tcount * 4,
+                                    cudaMemcpyHostToDevice, s->cs);
+    if (e == cudaSuccess && h.n_payload)
+        e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
+                            h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.counters, 0, L.total - L.counters, s->cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        wv_close_stream(s);
+        return WV_ERR_CUDA;
+    }
+    *out = s;
+    return WV_OK;
+}
+
+int wv_set_cuda_stream(wv_stream *s, void *cuda_stream) {
+    if (!s) return WV_ERR_ARG;
+    s->cs = (cudaStream_t)cuda_stream;
+    return WV_OK;
+}
+
+void wv_close_stream(wv_stream *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->cs);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    if (s->owns && s->dmem) cudaFree(s->dmem);
+    delete s;
+}
+
+int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
+                       const wv_image *out) {
+    return decode_viewport(s, frame, yaw, pitch, fov, out);
+}
+
+int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream) {
+    if (n < 0 || (n > 0 && !reqs)) return WV_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!reqs[i].s) return WV_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        wv_stream *s = reqs[i].s;
+        cudaStream_t saved = s->cs;
+        s->cs = (cudaStream_t)cuda_stream;
+        const int rc = decode_viewport(s, reqs[i].frame, reqs[i].yaw, reqs[i].pitch, reqs[i].fov,
+                                       &reqs[i].out);
+        s->cs = saved;
+        if (rc != WV_OK) return rc;
+    }
+    return WV_OK;
+}
+
+int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float) {
+    if (!s || frame < 0 || frame >= s->g.num_frames || plane < 0 || plane >= s->g.planes)
+        return WV_ERR_ARG;
+    if (!dptr && as_float) return WV_ERR_ARG;
+    const Geom &g = s->g;
+    uint8_t *outs[3] = {s->recon[0], s->recon[1], s->recon[2]};
+    float *f32 = nullptr;
+    if (dptr) {
+        if (as_float) f32 = (float *)dptr;
+        else outs[plane] = (uint8_t *)dptr;
+    }
+    launch_all_tiles(g, plane, s->tiles, s->counters, s->cs);
+    cudaError_t e = launch_decode_tiles(g, s->payload, s->table, frame_bands(g, frame), outs, f32,
+                                        as_float ? plane : -1, s->tiles, s->counters, s->err, s->cs);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    return cuda_err(cudaGetLastError());
+}
+
+int wv_stream_sync_status(wv_stream *s) {
+    if (!s) return WV_ERR_ARG;
+    if (cudaStreamSynchronize(s->cs) != cudaSuccess) return WV_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, s->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return WV_ERR_CUDA;
+    if (err) cudaMemset(s->err, 0, 4);
+    return err;
+}
+
+int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_w, int out_h,
+                       uint8_t *mask_host, int *tiles) {
+    if (!s || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f)) return WV_ERR_ARG;
+    const Geom &g = s->g;
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
+    uint8_t *m = s->mask[s->mask_parity];
+    uint8_t *other = s->mask[s->mask_parity ^ 1];
+    launch_footprint(g, v, m, s->counters, s->cs);
+    launch_select_tiles(g, m, other, s->tiles, s->counters, s->cs);
+    s->mask_parity ^= 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mask_host)
+        e = cudaMemcpyAsync(mask_host, m, (size_t)g.cells_x * g.cells_y, cudaMemcpyDeviceToHost, s->cs);
+    int cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, s->counters, 4, cudaMemcpyDeviceToHost, s->cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+    if (tiles) *tiles = cnt;
+    return cuda_err(e);
+}
+
+int wv_debug_project(wv_stream *s, float yaw, float pitch, float fov, int out_w, int out_h,
+                     float *uv_dev) {
+    if (!s || !uv_dev || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f))
+        return WV_ERR_ARG;
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, s->g.p[0].w, s->g.p[0].h);
+    launch_project(v, uv_dev, s->cs);
+    return cuda_err(cudaGetLastError());
+}
+
+int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
+    if (!s || !uv_dev || check_image(out) != WV_OK) return WV_ERR_ARG;
+    View v = make_view(0.f, 0.f, 1.f, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
+    launch_resample(s->g, v, s->recon, uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
+    return cuda_err(cudaGetLastError());
+}
+
+int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host, unsigned long long *bytes) {
+    if (!s || !mask_host || !bytes || frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
+    *bytes = cone_bytes(s, frame, mask_host);
+    return WV_OK;
+}
+
+int wv_profile_begin(wv_stream *s) {
+    if (!s) return WV_ERR_ARG;
+    s->prof = true;
+    s->ev_used = 0;
+    s->ev_kind.clear();
+    return WV_OK;
+}
+
+int wv_profile_end(wv_stream *s, wv_profile *out) {
+    if (!s || !out) return WV_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (cudaStreamSynchronize(s->cs) != cudaSuccess) return WV_ERR_CUDA;
+    for (size_t i = 0; i < s->ev_kind.size(); ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
+        const int k = s->ev_kind[i];
+        out->ms[k] += ms;
+        out->launches[k] += 1;
+    }
+    int cnt = 0;
+    cudaMemcpy(&cnt, s->counters, 4, cudaMemcpyDeviceToHost);
+    out->tiles = cnt;
+    s->prof = false;
+    s->ev_used = 0;
+    s->ev_kind.clear();
+    return WV_OK;
+}
+
+int wv_launches_per_viewport(void) { return kLaunchesPerViewport; }
+
+int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes, size_t *max_stream_bytes) {
+    if (!desc) return WV_ERR_ARG;
+    Geom g;
+    if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
+    return encode_sizes(g, scratch_bytes, max_stream_bytes);
+}
+
+int wv_encode(const wv_stream_desc *desc, const void *const *planes_dev, void *scratch_dev,
+              size_t scratch_bytes, void *out, size_t cap, size_t *out_len, void *cuda_stream) {
+    if (!desc || !planes_dev || !scratch_dev || !out || !out_len) return WV_ERR_ARG;
+    Geom g;
+    if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
+    return encode_run(g, planes_dev, scratch_dev, scratch_bytes, out, cap, out_len,
+                      (cudaStream_t)cuda_stream);
+}
+
+}  // extern "C"

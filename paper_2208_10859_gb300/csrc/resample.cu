@@ -1,0 +1,112 @@
+// resample.cu -- reprojection of the decoded equirectangular region into the
+// viewport (Sec. 3.6: a mapping pass after the inverse wavelet transform) and
+// YCbCr -> RGBA conversion.
+//
+// Per viewport pixel: the same projection as the footprint kernel gives the
+// luma position (u, v); u wraps around the longitude seam, v clamps at the
+// poles.  Bilinear filtering in fixed point: the fraction is rounded to 1/256
+// (half up, with carry), the four integer weights sum to 65536 and the result
+// is (sum + 32768) >> 16.  Chroma (4:2:0, centre-sited) is sampled at
+// ((u + 1/2) / 2 - 1/2, (v + 1/2) / 2 - 1/2).  Colour: BT.709 full range,
+// coefficients rounded to 1/65536, result rounded half up and clamped.
+// The paper itself stores no colour transform (Sec. 5); the YCbCr 4:2:0
+// stream and this conversion belong to this decoder's format.
+#include "wv_impl.h"
+
+namespace wv {
+
+namespace {
+
+// BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb.
+constexpr double kKr = 0.2126, kKb = 0.0722, kKg = 1.0 - kKr - kKb;
+constexpr int kRCr = (int)(2.0 * (1.0 - kKr) * 65536.0 + 0.5);
+constexpr int kGCb = (int)(2.0 * kKb * (1.0 - kKb) / kKg * 65536.0 + 0.5);
+constexpr int kGCr = (int)(2.0 * kKr * (1.0 - kKr) / kKg * 65536.0 + 0.5);
+constexpr int kBCb = (int)(2.0 * (1.0 - kKb) * 65536.0 + 0.5);
+
+__device__ __forceinline__ int bilinear_u8(const uint8_t *__restrict__ img, int w, int h,
+                                           float u, float v) {
+    int x0, fx, y0, fy;
+    fixed_split(u, x0, fx);
+    fixed_split(v, y0, fy);
+    int xa = x0 % w;
+    if (xa < 0) xa += w;
+    const int xb = (xa + 1 == w) ? 0 : xa + 1;
+    const int ya = min(max(y0, 0), h - 1);
+    const int yb = min(max(y0 + 1, 0), h - 1);
+    const int p00 = __ldg(img + (size_t)ya * w + xa), p01 = __ldg(img + (size_t)ya * w + xb);
+    const int p10 = __ldg(img + (size_t)yb * w + xa), p11 = __ldg(img + (size_t)yb * w + xb);
+    const int acc = (256 - fx) * (256 - fy) * p00 + fx * (256 - fy) * p01 +
+                    (256 - fx) * fy * p10 + fx * fy * p11;
+    return (acc + 32768) >> 16;
+}
+
+__device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {
+    const int yy = y * 65536 + 32768;
+    cb -= 128;
+    cr -= 128;
+    const int r = (yy + kRCr * cr) >> 16;
+    const int g = (yy - kGCb * cb - kGCr * cr) >> 16;
+    const int b = (yy + kBCb * cb) >> 16;
+    return make_uchar4((unsigned char)min(max(r, 0), 255), (unsigned char)min(max(g, 0), 255),
+                       (unsigned char)min(max(b, 0), 255), 255);
+}
+
+struct ResampleArgs {
+    View v;
+    const uint8_t *plane[3];
+    int w[3], h[3];
+    int planes, c420;
+    const float *uv;   // optional caller-given positions
+    uint8_t *out;
+    size_t pitch;
+};
+
+__global__ void k_resample(ResampleArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.v.out_w || j >= a.v.out_h) return;
+    float u, v;
+    if (a.uv) {
+        const float2 p = reinterpret_cast<const float2 *>(a.uv)[(size_t)j * a.v.out_w + i];
+        u = p.x;
+        v = p.y;
+    } else {
+        project_px(a.v, i, j, u, v);
+    }
+    const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
+    int cb = 128, cr = 128;
+    if (a.planes == 3) {
+        float uc = u, vc = v;
+        if (a.c420) {
+            uc = fmaf(u + 0.5f, 0.5f, -0.5f);
+            vc = fmaf(v + 0.5f, 0.5f, -0.5f);
+        }
+        cb = bilinear_u8(a.plane[1], a.w[1], a.h[1], uc, vc);
+        cr = bilinear_u8(a.plane[2], a.w[2], a.h[2], uc, vc);
+    }
+    reinterpret_cast<uchar4 *>(a.out + (size_t)j * a.pitch)[i] = to_rgba(y, cb, cr);
+}
+
+}  // namespace
+
+void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
+                     uint8_t *out, size_t pitch, cudaStream_t cs) {
+    ResampleArgs a;
+    a.v = v;
+    for (int p = 0; p < 3; ++p) {
+        a.plane[p] = recon[p];
+        a.w[p] = p < g.planes ? g.p[p].w : 0;
+        a.h[p] = p < g.planes ? g.p[p].h : 0;
+    }
+    a.planes = g.planes;
+    a.c420 = g.c420;
+    a.uv = uv;
+    a.out = out;
+    a.pitch = pitch;
+    dim3 block(32, 8);
+    dim3 grid((v.out_w + 31) / 32, (v.out_h + 7) / 8);
+    k_resample<<<grid, block, 0, cs>>>(a);
+}
+
+}  // namespace wv

@@ -1,0 +1,278 @@
+"""Thin Python binding of the C ABI in include/wv.h (ctypes).
+
+Argument marshalling only: every step of the decode runs in libwv.so's CUDA
+kernels.  PyTorch supplies device memory (tensors) and CUDA streams.  There
+is no CPU fallback: importing this module on a machine without the built
+library raises, and calls without a CUDA device return WV_ERR_CUDA.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+WV_OK = 0
+ERRORS = {-1: "WV_ERR_ARG", -2: "WV_ERR_FORMAT", -3: "WV_ERR_OOM", -4: "WV_ERR_CUDA",
+          -5: "WV_ERR_RANGE", -6: "WV_ERR_TIMEOUT", -7: "WV_ERR_DEVICE"}
+WAVELET_53 = 0
+WAVELET_97 = 1
+
+
+class WVError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({_lib().wv_strerror(code).decode()})")
+
+
+class StreamDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("planes", ctypes.c_int),
+                ("chroma_420", ctypes.c_int), ("levels", ctypes.c_int), ("wavelet", ctypes.c_int),
+                ("num_frames", ctypes.c_int), ("tlevels", ctypes.c_int), ("block", ctypes.c_int),
+                ("quant", ctypes.c_int), ("step", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("dptr", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("pitch_bytes", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_void_p), ("frame", ctypes.c_int), ("yaw", ctypes.c_float),
+                ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int * 8), ("tiles", ctypes.c_int)]
+
+
+KERNEL_NAMES = ["footprint", "select_tiles", "decode_tiles", "resample"]
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libwv.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        c_int, c_size, vp, fl = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_float
+        sig = {
+            "wv_strerror": (ctypes.c_char_p, [c_int]),
+            "wv_stream_query": (c_int, [vp, c_size, ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size)]),
+            "wv_open_stream": (c_int, [vp, c_size, vp, c_size, vp, ctypes.POINTER(vp)]),
+            "wv_set_cuda_stream": (c_int, [vp, vp]),
+            "wv_close_stream": (None, [vp]),
+            "wv_decode_viewport": (c_int, [vp, c_int, fl, fl, fl, ctypes.POINTER(Image)]),
+            "wv_decode_batch": (c_int, [ctypes.POINTER(Request), c_int, vp]),
+            "wv_decode_full": (c_int, [vp, c_int, c_int, vp, c_int]),
+            "wv_stream_sync_status": (c_int, [vp]),
+            "wv_debug_footprint": (c_int, [vp, fl, fl, fl, c_int, c_int, vp, ctypes.POINTER(c_int)]),
+            "wv_debug_project": (c_int, [vp, fl, fl, fl, c_int, c_int, vp]),
+            "wv_resample_at": (c_int, [vp, vp, ctypes.POINTER(Image)]),
+            "wv_cone_bytes": (c_int, [vp, c_int, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+            "wv_profile_begin": (c_int, [vp]),
+            "wv_profile_end": (c_int, [vp, ctypes.POINTER(Profile)]),
+            "wv_launches_per_viewport": (c_int, []),
+            "wv_encode_sizes": (c_int, [ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size), ctypes.POINTER(c_size)]),
+            "wv_encode": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, vp, c_size,
+                                  ctypes.POINTER(c_size), vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols() -> list[str]:
+    """Names of the ABI functions the binding resolves (all of include/wv.h)."""
+    _lib()
+    return ["wv_strerror", "wv_stream_query", "wv_open_stream", "wv_set_cuda_stream",
+            "wv_close_stream", "wv_decode_viewport", "wv_decode_batch", "wv_decode_full",
+            "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
+            "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
+            "wv_encode_sizes", "wv_encode"]
+
+
+def _check(rc: int, what: str):
+    if rc != WV_OK:
+        raise WVError(rc, what)
+
+
+def _cuda_stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _image(t) -> Image:
+    import torch
+    if not (t.is_cuda and t.dtype == torch.uint8 and t.dim() == 3 and t.shape[2] == 4):
+        raise ValueError("output must be a CUDA uint8 tensor of shape (H, W, 4)")
+    if t.stride(2) != 1 or t.stride(1) != 4:
+        raise ValueError("output rows must be packed RGBA")
+    return Image(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0))
+
+
+def query(data: bytes) -> tuple[dict, int]:
+    d = StreamDesc()
+    need = ctypes.c_size_t()
+    buf = ctypes.c_char_p(data)
+    _check(_lib().wv_stream_query(buf, len(data), ctypes.byref(d), ctypes.byref(need)), "wv_stream_query")
+    return d.as_dict(), need.value
+
+
+class Stream:
+    """An open wavelet video stream resident on the GPU."""
+
+    def __init__(self, data: bytes, cuda_stream=None):
+        import torch
+        self.desc, need = query(data)
+        # device store supplied by PyTorch's allocator (256-byte aligned)
+        self._mem = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        base = self._mem.data_ptr()
+        aligned = (base + 255) & ~255
+        self._handle = ctypes.c_void_p()
+        self._cuda_stream = cuda_stream
+        _check(_lib().wv_open_stream(ctypes.c_char_p(data), len(data), ctypes.c_void_p(aligned), need,
+                                     ctypes.c_void_p(_cuda_stream_handle(cuda_stream)),
+                                     ctypes.byref(self._handle)), "wv_open_stream")
+        self.device_bytes = need
+
+    @property
+    def handle(self) -> int:
+        return self._handle.value
+
+    def set_cuda_stream(self, stream) -> None:
+        self._cuda_stream = stream
+        _check(_lib().wv_set_cuda_stream(self._handle, ctypes.c_void_p(_cuda_stream_handle(stream))),
+               "wv_set_cuda_stream")
+
+    def decode_viewport(self, frame: int, yaw: float, pitch: float, fov: float, out) -> None:
+        img = _image(out)
+        _check(_lib().wv_decode_viewport(self._handle, frame, yaw, pitch, fov, ctypes.byref(img)),
+               "wv_decode_viewport")
+
+    def decode_full(self, frame: int, plane: int, out=None, as_float: bool = False) -> None:
+        ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
+        _check(_lib().wv_decode_full(self._handle, frame, plane, ptr, int(as_float)), "wv_decode_full")
+
+    def sync_status(self) -> int:
+        return _lib().wv_stream_sync_status(self._handle)
+
+    def debug_footprint(self, yaw, pitch, fov, out_w, out_h):
+        d = self.desc
+        mask = np.zeros((d["height"] // 32, d["width"] // 32), np.uint8)
+        tiles = ctypes.c_int()
+        _check(_lib().wv_debug_footprint(self._handle, yaw, pitch, fov, out_w, out_h,
+                                         mask.ctypes.data_as(ctypes.c_void_p), ctypes.byref(tiles)),
+               "wv_debug_footprint")
+        return mask, tiles.value
+
+    def debug_project(self, yaw, pitch, fov, out_w, out_h):
+        import torch
+        uv = torch.empty((out_h, out_w, 2), dtype=torch.float32, device="cuda")
+        _check(_lib().wv_debug_project(self._handle, yaw, pitch, fov, out_w, out_h,
+                                       ctypes.c_void_p(uv.data_ptr())), "wv_debug_project")
+        return uv
+
+    def resample_at(self, uv, out) -> None:
+        img = _image(out)
+        if not (uv.is_cuda and uv.is_contiguous() and tuple(uv.shape) == (out.shape[0], out.shape[1], 2)
+                and str(uv.dtype) == "torch.float32"):
+            raise ValueError("uv must be a contiguous CUDA float32 tensor of shape (H, W, 2)")
+        _check(_lib().wv_resample_at(self._handle, ctypes.c_void_p(uv.data_ptr()), ctypes.byref(img)),
+               "wv_resample_at")
+
+    def cone_bytes(self, frame: int, mask: np.ndarray) -> int:
+        m = np.ascontiguousarray(mask, np.uint8)
+        out = ctypes.c_ulonglong()
+        _check(_lib().wv_cone_bytes(self._handle, frame, m.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.byref(out)), "wv_cone_bytes")
+        return out.value
+
+    def profile_begin(self) -> None:
+        _check(_lib().wv_profile_begin(self._handle), "wv_profile_begin")
+
+    def profile_end(self) -> dict:
+        p = Profile()
+        _check(_lib().wv_profile_end(self._handle, ctypes.byref(p)), "wv_profile_end")
+        out = {n: (p.ms[i], p.launches[i]) for i, n in enumerate(KERNEL_NAMES)}
+        out["tiles"] = p.tiles
+        return out
+
+    def close(self) -> None:
+        if self._handle.value:
+            _lib().wv_close_stream(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class ViewRequest:
+    stream: Stream
+    frame: int
+    yaw: float
+    pitch: float
+    fov: float
+    out: object
+
+
+def decode_batch(requests: list, cuda_stream=None) -> None:
+    arr = (Request * len(requests))()
+    for i, r in enumerate(requests):
+        arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out))
+    _check(_lib().wv_decode_batch(arr, len(requests), ctypes.c_void_p(_cuda_stream_handle(cuda_stream))),
+           "wv_decode_batch")
+
+
+def launches_per_viewport() -> int:
+    return _lib().wv_launches_per_viewport()
+
+
+def encode(frames, desc: dict, cuda_stream=None) -> bytes:
+    """Encode frames (list of num_frames tuples of CUDA uint8 plane tensors) on
+    the GPU into stream bytes."""
+    import torch
+    d = StreamDesc(**{k: desc.get(k, 0) for k, _ in StreamDesc._fields_})
+    scratch = ctypes.c_size_t()
+    cap = ctypes.c_size_t()
+    _check(_lib().wv_encode_sizes(ctypes.byref(d), ctypes.byref(scratch), ctypes.byref(cap)), "wv_encode_sizes")
+    mem = torch.empty(scratch.value + 256, dtype=torch.uint8, device="cuda")
+    base = (mem.data_ptr() + 255) & ~255
+    ptrs = []
+    keep = []
+    for fr in frames:
+        for p in fr:
+            t = p.contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    out = np.empty(cap.value, np.uint8)
+    n = ctypes.c_size_t()
+    torch.cuda.current_stream().synchronize()
+    _check(_lib().wv_encode(ctypes.byref(d), arr, ctypes.c_void_p(base), scratch.value,
+                            out.ctypes.data_as(ctypes.c_void_p), cap.value, ctypes.byref(n),
+                            ctypes.c_void_p(_cuda_stream_handle(cuda_stream))), "wv_encode")
+    del mem, keep
+    return out[:n.value].tobytes()

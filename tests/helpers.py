@@ -1,0 +1,137 @@
+"""Shared seeded workloads and comparison helpers for the tests.
+
+Streams are always produced by the oracle encoder from synth frames, so no
+oracle input ever comes from the CUDA path."""
+from __future__ import annotations
+
+import functools
+import math
+
+import numpy as np
+
+import oracle as O
+import synth
+
+# name -> (frame builder, Params)
+CASES = {
+    # the lossless workload: 512x512 grey, 3-level LeGall 5/3, step 1
+    "cfg1": (lambda: [(synth.gradient_rects_frame(512, seed=1),)],
+             O.Params(512, 512, 1, 0, 3, O.WAVELET_53, 1, 0, 256, 1.0)),
+    # YCbCr 4:2:0, 5/3 lossless, inter-frame sets of 4 (two Haar levels)
+    "yuv53": (lambda: synth.equirect_gop(256, 4, seed=21, n_discs=6),
+              O.Params(256, 256, 3, 1, 3, O.WAVELET_53, 4, 2, 64, 1.0)),
+    # YCbCr 4:2:0, 9/7, one Haar level over pairs, dead-zone step 4
+    "yuv97": (lambda: synth.equirect_gop(256, 4, seed=22, n_discs=6),
+              O.Params(256, 256, 3, 1, 4, O.WAVELET_97, 4, 1, 64, 4.0)),
+    # grey 9/7 at the maximum level count with the smallest block size and
+    # three Haar levels (sets of 8 frames)
+    "gray97_L6": (lambda: synth.equirect_gop(512, 8, seed=24, n_discs=5, chroma=False),
+                  O.Params(512, 512, 1, 0, 6, O.WAVELET_97, 8, 3, 16, 1.0)),
+}
+
+
+def _ragged_frames(n, seed):
+    """Non-square 320 x 192 YCbCr frames (equirect drawing cropped)."""
+    fr = synth.equirect_gop(320, n, seed=seed, n_discs=4)
+    return [tuple(np.ascontiguousarray(p[: p.shape[0] * 192 // 320]) for p in f) for f in fr]
+
+
+# ragged: 320 x 192 is not a multiple of the 128-pixel tile (partial tiles,
+# non-square planes); 5/3 with an integer step of 3, 9/7 with step 2
+CASES["ragged53"] = (lambda: _ragged_frames(2, 23),
+                     O.Params(320, 192, 3, 1, 2, O.WAVELET_53, 2, 1, 32, 3.0))
+CASES["ragged97"] = (lambda: _ragged_frames(2, 25),
+                     O.Params(320, 192, 3, 1, 4, O.WAVELET_97, 2, 1, 32, 2.0))
+
+
+@functools.lru_cache(maxsize=None)
+def case(name: str):
+    """(frames, params, stream bytes, oracle Stream) of a named workload."""
+    build, p = CASES[name]
+    frames = build()
+    data = O.encode(frames, p)
+    return frames, p, data, O.Stream(data)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_planes(name: str, frame: int):
+    """Oracle reconstruction of every plane of a frame: list of (x, u8)."""
+    _, p, _, st = case(name)
+    return [O.decode_plane(st, frame, pl) for pl in range(p.planes)]
+
+
+def tol_97_levels() -> float:
+    """Bound on |float32 decode - fp64 oracle| for 9/7 samples: 1e-4 of the
+    8-bit full scale (samples normalised to [0, 1])."""
+    return 1e-4 * 255.0
+
+
+def near_half(x: np.ndarray, eps: float = 2e-3) -> np.ndarray:
+    """Samples whose exact value is within eps of a rounding boundary k + 1/2
+    (where float32 and fp64 may round to different 8-bit values)."""
+    f = x - np.floor(x)
+    return np.abs(f - 0.5) < eps
+
+
+def other_rounding(x: np.ndarray, eps: float = 2e-3) -> np.ndarray:
+    """8-bit planes where every sample within eps of a rounding boundary takes
+    the rounding the oracle did not choose; all others as the oracle rounds."""
+    r = np.floor(x + 0.5)
+    alt = np.where(x - np.floor(x) < 0.5, r + 1, r - 1)
+    return np.clip(np.where(near_half(x, eps), alt, r), 0, 255).astype(np.uint8)
+
+
+def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov):
+    """Per-pixel bound (eps_u, eps_v) in pixels on the float32 position error
+    of the device projection: direction components carry a few float32
+    rounding errors (~4e-7 relative), atan2f adds at most 2 ulp, and the
+    longitude error is amplified by 1/cos(latitude) near the poles; a final
+    rounding of u (v) adds half an ulp of the frame width (height)."""
+    t = math.tan(fov / 2)
+    xn = (2 * (np.arange(out_w) + 0.5) / out_w - 1) * t
+    yn = (1 - 2 * (np.arange(out_h) + 0.5) / out_h) * t
+    X, Y = np.meshgrid(xn, yn)
+    cam = np.stack([X, Y, np.ones_like(X)], -1)
+    d = cam @ O.rotation(yaw, pitch).T
+    norm = np.linalg.norm(d, axis=-1)
+    coslat = np.hypot(d[..., 0], d[..., 2]) / norm
+    ku = p.width / (2 * math.pi)
+    kv = p.height / math.pi
+    eps_u = ku * (1.5e-6 / np.maximum(coslat, 1e-9) + 5e-7) + p.width * 2.0 ** -23
+    eps_v = np.full_like(eps_u, kv * 1.5e-6 + p.height * 2.0 ** -23)
+    return eps_u, eps_v
+
+
+def quanta(t: np.ndarray, eps, k: int = 4):
+    """Up to k candidate positions q/256 whose 1/256 quantisation a value in
+    [t - eps, t + eps] may take; second result flags values needing more."""
+    lo = np.floor((t - eps) * 256 + 0.5)
+    hi = np.floor((t + eps) * 256 + 0.5)
+    qs = [np.minimum(lo + i, hi) / 256.0 for i in range(k)]
+    return np.stack(qs, -1), (hi - lo + 1) > k
+
+
+def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v):
+    """Candidate RGBA values (n, k*k*k*k, 4) for sampled pixels whose exact
+    positions are (u, v) +- (eps_u, eps_v); also a flag for pixels that need
+    more than k quanta per axis (excluded from the check)."""
+    qu, fu = quanta(u, eps_u)
+    qv, fv = quanta(v, eps_v)
+    n, k = u.shape[0], qu.shape[1]
+    Yc = np.stack([O.bilinear(planes[0], qu[:, a], qv[:, b]) for a in range(k) for b in range(k)], -1)
+    if p.planes == 3:
+        uc, vc = O.chroma_coords(u, v)
+        quc, fuc = quanta(uc, eps_u / 2)
+        qvc, fvc = quanta(vc, eps_v / 2)
+        Cb = np.stack([O.bilinear(planes[1], quc[:, a], qvc[:, b]) for a in range(k) for b in range(k)], -1)
+        Cr = np.stack([O.bilinear(planes[2], quc[:, a], qvc[:, b]) for a in range(k) for b in range(k)], -1)
+        flag = fu | fv | fuc | fvc
+    else:
+        Cb = np.full_like(Yc, 128)
+        Cr = np.full_like(Yc, 128)
+        flag = fu | fv
+    m = Yc.shape[1]
+    Yx = np.repeat(Yc, m, axis=1)
+    Cbx = np.tile(Cb, (1, m))
+    Crx = np.tile(Cr, (1, m))
+    return O.ycbcr_to_rgba(Yx, Cbx, Crx), flag

@@ -1,0 +1,97 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+function include/wv.h declares, validates stream bytes, and refuses to run
+without a CUDA device instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+import struct
+
+import pytest
+
+import oracle as O
+import helpers as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_10859_gb300 import build, wv
+    build.build()
+    return wv._lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "wv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wv_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2208_10859_gb300 import wv
+    assert sorted(wv.exported_symbols()) == names
+
+
+def test_strerror_names_every_code(lib):
+    for code in range(0, -8, -1):
+        assert lib.wv_strerror(code).decode() not in ("", "unknown error")
+    assert lib.wv_strerror(-99).decode() == "unknown error"
+
+
+def test_query_parses_oracle_streams(lib):
+    from paper_2208_10859_gb300 import wv
+    for name in ("cfg1", "yuv97", "ragged53"):
+        _, p, data, _ = H.case(name)
+        desc, need = wv.query(data)
+        assert (desc["width"], desc["height"], desc["planes"], desc["levels"], desc["wavelet"],
+                desc["num_frames"], desc["tlevels"], desc["block"]) == \
+            (p.width, p.height, p.planes, p.levels, p.wavelet, p.num_frames, p.tlevels, p.block)
+        assert need >= len(data) - 128
+
+
+def test_query_rejects_corrupt_streams(lib):
+    from paper_2208_10859_gb300 import wv
+    _, _, data, _ = H.case("yuv97")
+    bad_cases = [data[:100], b"XXXX" + data[4:], data[: len(data) // 2]]
+    toff = struct.unpack_from("<Q", data, 72)[0]
+    b = bytearray(data)
+    struct.pack_into("<i", b, toff + 8, 10 ** 6)          # slot beyond the payload
+    bad_cases.append(bytes(b))
+    b = bytearray(data)
+    struct.pack_into("<I", b, 24, 9)                       # 9 levels: unsupported
+    bad_cases.append(bytes(b))
+    b = bytearray(data)
+    struct.pack_into("<I", b, 40, 48)                      # block not a power of two
+    bad_cases.append(bytes(b))
+    for bad in bad_cases:
+        with pytest.raises(wv.WVError) as e:
+            wv.query(bad)
+        assert e.value.code == -2
+
+
+def test_open_without_gpu_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    _, _, data, _ = H.case("cfg1")
+    h = ctypes.c_void_p()
+    rc = lib.wv_open_stream(ctypes.c_char_p(data), len(data), None, 0, None, ctypes.byref(h))
+    assert rc == -4 and not h.value
+
+
+def test_encode_sizes(lib):
+    from paper_2208_10859_gb300 import wv
+    d = wv.StreamDesc(8192, 8192, 3, 1, 5, 1, 8, 1, 256, 0, 4.0)
+    scratch, cap = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.wv_encode_sizes(ctypes.byref(d), ctypes.byref(scratch), ctypes.byref(cap)) == 0
+    assert cap.value >= 8 * 1536 * 256 * 256 * 2
+    d.levels = 7
+    assert lib.wv_encode_sizes(ctypes.byref(d), ctypes.byref(scratch), ctypes.byref(cap)) == -1
+
+
+def test_launch_count(lib):
+    assert lib.wv_launches_per_viewport() == 4
