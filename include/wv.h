@@ -163,6 +163,32 @@ int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream);
  * reconstruction plane (as uint8) for wv_resample_at. */
 int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float);
 
+/* Decode one whole plane without allocating any device memory.  The paper
+ * has no counterpart: this entry point exists for callers that must not
+ * allocate GPU memory themselves -- for example a plug-in whose host
+ * application owns every device allocation -- but already hold a stream's
+ * block table (int32 [num_frames][blocks per frame], the stream's table) and
+ * coefficient payload (int16 blocks) in device memory they own.
+ * desc describes the stream (host memory).  out_dev receives the plane's
+ * width x height samples, row-major and tightly packed: uint8 (as_float = 0)
+ * or float32 before rounding (as_float = 1), as in wv_decode_full.  Work is
+ * enqueued on cuda_stream (NULL = legacy default stream) and the call returns
+ * before it finishes.
+ * Scratch: the tile list and counters live in one static device array of
+ * 16 KB + 256 bytes that every GPU loading the library holds until the
+ * process exits; planes of more than 4096 tiles of 128 x 128 samples (larger
+ * than 8192 x 8192) are rejected with WV_ERR_RANGE.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Table entries must lie in [-1, number of payload blocks); they are not
+ * checked on the device.  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+int wv_decode_plane_static(const wv_stream_desc *desc, const void *payload_dev,
+                           const void *table_dev, int frame, int plane, void *out_dev,
+                           int as_float, void *cuda_stream);
+
 /* Wait for the stream's CUDA stream and read the device error word: WV_OK,
  * or the first error a kernel recorded since the previous call (the word is
  * then cleared). */

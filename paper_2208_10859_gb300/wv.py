@@ -89,6 +89,8 @@ def _lib():
             "wv_encode_sizes": (c_int, [ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size), ctypes.POINTER(c_size)]),
             "wv_encode": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, vp, c_size,
                                   ctypes.POINTER(c_size), vp]),
+            "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
+                                               c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -105,7 +107,7 @@ def exported_symbols() -> list[str]:
             "wv_close_stream", "wv_decode_viewport", "wv_decode_batch", "wv_decode_full",
             "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
-            "wv_encode_sizes", "wv_encode"]
+            "wv_encode_sizes", "wv_encode", "wv_decode_plane_static"]
 
 
 def _check(rc: int, what: str):
