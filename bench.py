@@ -274,7 +274,15 @@ def run_ours(args):
     for _ in range(args.steps):
         step()
     prof = s.profile_end()
-    dec_ms, dec_n = prof["decode_tiles"]
+    dec_ms = prof["decode_coarse"][0] + prof["decode_fine"][0]
+    dec_n = prof["decode_fine"][1]
+    # the other tile-decode organisation (all levels fused per tile), for comparison
+    s.set_decode_mode(1)
+    s.profile_begin()
+    step()
+    prof_fused = s.profile_end()
+    s.set_decode_mode(0)
+    fused_ms = prof_fused["decode_fine"][0] / max(1, prof_fused["decode_fine"][1])
     alg_dec = sum(cone) + sum(region)   # per pass over the poses
     achieved = alg_dec * args.steps / (dec_ms / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
@@ -332,18 +340,20 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2: coded group {len(data) / 1e9:.2f} GB device-resident",
                        "stream_bytes": len(data)},
-            "gpu_launches": args.steps * len(poses) * wv.launches_per_viewport(),
+            "gpu_launches": args.steps * len(poses) * s.launches_per_viewport(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(data),
                     "d2h_bytes_per_step": len(poses) * out_bytes,
                     "note": "per step: wv_open_stream from pinned host bytes, 64 wv_decode_viewport, "
                             "64 RGBA reads to pinned host memory"},
-            "roofline": {"kernel": "decode_tiles", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "tile decode (k_tiles coarse + fine passes)", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None if trec is None else trec["traffic_bytes_per_launch"],
                          "algorithmic_bytes_per_launch": alg_dec / len(poses),
                          "avg_launch_ms": dec_ms / max(1, dec_n)},
             "kernel_ms_per_launch": kernel_ms,
+            "decode_ms_per_viewport": {"split (coarse + fine)": dec_ms / max(1, dec_n),
+                                       "fused (all levels per tile)": fused_ms},
             "viewport_bytes": {"cone_coef_mean": sum(cone) / len(cone), "region_mean": sum(region) / len(region),
                                "rgba": out_bytes,
                                "whole_path_alg_GBps": (sum(cone) + len(poses) * out_bytes) * args.steps / (ms / 1e3) / 1e9},

@@ -228,7 +228,7 @@ int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
  * measured with CUDA events recorded on the stream's CUDA stream around
  * each launch. */
 typedef struct {
-    double ms[8];        /* footprint, tiles, decode tiles, resample, ... */
+    double ms[8];        /* footprint, select tiles, coarse decode, fine decode, resample */
     int launches[8];
     int tiles;           /* tiles decoded by the last viewport */
 } wv_profile;
@@ -237,8 +237,16 @@ int wv_profile_begin(wv_stream *s);
 /* Synchronises, sums the recorded event intervals into *out and stops. */
 int wv_profile_end(wv_stream *s, wv_profile *out);
 
-/* Number of kernel launches a wv_decode_viewport call makes. */
-int wv_launches_per_viewport(void);
+/* Number of kernel launches a wv_decode_viewport call on s makes. */
+int wv_launches_per_viewport(const wv_stream *s);
+
+/* Tile-decode organisation for streams of three or more levels: mode 0
+ * (default) decodes levels L..3 of the needed coarse tiles into float LL_2
+ * planes in one kernel and levels 2..1 of the needed output tiles in a
+ * second; mode 1 runs all levels of each output tile in one kernel, repeating
+ * the coarse levels per tile.  Results are identical up to float rounding
+ * order for 9/7 and bit-exact for 5/3. */
+int wv_set_decode_mode(wv_stream *s, int mode);
 
 /* ---------------------------------------------------------------------------
  * Encoder (offline; not part of the decode path)

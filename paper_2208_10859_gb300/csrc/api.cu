@@ -29,8 +29,9 @@ using namespace wv;
 
 namespace {
 
-enum Kernel { kKFootprint = 0, kKTiles = 1, kKDecode = 2, kKResample = 3 };
-constexpr int kLaunchesPerViewport = 4;
+enum Kernel { kKFootprint = 0, kKTiles = 1, kKCoarse = 2, kKFine = 3, kKResample = 4 };
+
+bool split_mode(const wv_stream *s) { return s->decode_mode == 0 && s->g.levels >= 3; }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -67,7 +68,7 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
 }
 
 struct Layout {
-    size_t payload, table, recon[3], mask[2], tiles, counters, err, total;
+    size_t payload, table, recon[3], ll2[3], mask[2], tiles, cflags, counters, err, total;
 };
 
 Layout layout(const Geom &g, uint64_t n_payload) {
@@ -81,12 +82,19 @@ Layout layout(const Geom &g, uint64_t n_payload) {
         L.recon[p] = o;
         if (p < g.planes) o = align256(o + (size_t)g.p[p].w * g.p[p].h);
     }
+    for (int p = 0; p < 3; ++p) {
+        L.ll2[p] = o;
+        if (p < g.planes && g.levels >= 3)
+            o = align256(o + (size_t)g.p[p].ll2_pitch * (g.p[p].h >> 2) * 4);
+    }
     for (int m = 0; m < 2; ++m) {
         L.mask[m] = o;
         o = align256(o + (size_t)g.cells_x * g.cells_y);
     }
     L.tiles = o;
     o = align256(o + (size_t)g.total_tiles * 4);
+    L.cflags = o;
+    o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1));
     L.counters = o;
     o = align256(o + 64);
     L.err = o;
@@ -124,6 +132,33 @@ int check_image(const wv_image *o) {
     return WV_OK;
 }
 
+// Tile decode of the selected tiles: a coarse pass (levels L..3 into LL_2
+// planes) followed by a fine pass (levels 2 and 1), or all levels in one
+// pass when the stream has fewer than three levels or mode 1 is set.
+cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, float *f32,
+                       int f32_plane) {
+    const Geom &g = s->g;
+    cudaError_t e;
+    if (split_mode(s)) {
+        prof_begin(s, kKCoarse);
+        e = launch_decode_coarse(g, s->payload, s->table, b, s->ll2, s->ll2_pitch, s->cflags,
+                                 s->err, s->cs);
+        prof_end(s);
+        if (e != cudaSuccess) return e;
+        const float *ll2c[3] = {s->ll2[0], s->ll2[1], s->ll2[2]};
+        prof_begin(s, kKFine);
+        e = launch_decode_fine(g, s->payload, s->table, b, ll2c, s->ll2_pitch, out_u8, f32,
+                               f32_plane, s->tiles, s->counters, s->err, s->cs);
+        prof_end(s);
+        return e;
+    }
+    prof_begin(s, kKFine);
+    e = launch_decode_tiles(g, s->payload, s->table, b, out_u8, f32, f32_plane, s->tiles,
+                            s->counters, s->err, s->cs);
+    prof_end(s);
+    return e;
+}
+
 int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
                     const wv_image *out) {
     if (!s) return WV_ERR_ARG;
@@ -139,13 +174,10 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     launch_footprint(g, v, m, s->counters, s->cs);
     prof_end(s);
     prof_begin(s, kKTiles);
-    launch_select_tiles(g, m, other, s->tiles, s->counters, s->cs);
+    launch_select_tiles(g, m, other, s->tiles, s->cflags, s->counters, s->cs);
     prof_end(s);
     s->mask_parity ^= 1;
-    prof_begin(s, kKDecode);
-    cudaError_t e = launch_decode_tiles(g, s->payload, s->table, b, s->recon, nullptr, -1,
-                                        s->tiles, s->counters, s->err, s->cs);
-    prof_end(s);
+    cudaError_t e = run_decode(s, b, s->recon, nullptr, -1);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     prof_begin(s, kKResample);
     launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
@@ -259,6 +291,7 @@ int build_geom(const wv_stream_desc &d, Geom *g) {
     g->cells_y = d.height / kCell;
     int id = 0;
     g->total_tiles = 0;
+    g->total_ctiles = 0;
     for (int p = 0; p < d.planes; ++p) {
         PlaneGeom &pg = g->p[p];
         pg.sub = (p > 0 && g->c420) ? 2 : 1;
@@ -282,6 +315,12 @@ int build_geom(const wv_stream_desc &d, Geom *g) {
         pg.tiles_x = (pg.w + kTile - 1) / kTile;
         pg.tiles_y = (pg.h + kTile - 1) / kTile;
         g->total_tiles += pg.tiles_x * pg.tiles_y;
+        pg.ll2_pitch = (((pg.w >> 2) + 7) / 8) * 8;
+        if (d.levels >= 3) {
+            pg.ctiles_x = ((pg.w >> 2) + kCoarseTile - 1) / kCoarseTile;
+            pg.ctiles_y = ((pg.h >> 2) + kCoarseTile - 1) / kCoarseTile;
+        }
+        g->total_ctiles += pg.ctiles_x * pg.ctiles_y;
     }
     g->nbpf = id;
     return WV_OK;
@@ -403,6 +442,12 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     s->mask[0] = (uint8_t *)(base + L.mask[0]);
     s->mask[1] = (uint8_t *)(base + L.mask[1]);
     s->tiles = (uint32_t *)(base + L.tiles);
+    s->cflags = (uint8_t *)(base + L.cflags);
+    for (int p = 0; p < 3; ++p) {
+        const bool has = p < s->g.planes && s->g.levels >= 3;
+        s->ll2[p] = has ? (float *)(base + L.ll2[p]) : nullptr;
+        s->ll2_pitch[p] = has ? s->g.p[p].ll2_pitch : 0;
+    }
     s->counters = (int *)(base + L.counters);
     s->err = (int *)(base + L.err);
     const size_t tcount = (size_t)s->g.num_frames * s->g.nbpf;
@@ -413,7 +458,8 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     if (e == cudaSuccess && h.n_payload)
         e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
                             h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.mask[0] - L.recon[0], s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.mask[0], 0, L.tiles - L.mask[0], s->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.counters, 0, L.total - L.counters, s->cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (e != cudaSuccess) {
@@ -472,8 +518,8 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
         else outs[plane] = (uint8_t *)dptr;
     }
     launch_all_tiles(g, plane, s->tiles, s->counters, s->cs);
-    cudaError_t e = launch_decode_tiles(g, s->payload, s->table, frame_bands(g, frame), outs, f32,
-                                        as_float ? plane : -1, s->tiles, s->counters, s->err, s->cs);
+    if (split_mode(s)) launch_all_ctiles(g, plane, s->cflags, s->cs);
+    cudaError_t e = run_decode(s, frame_bands(g, frame), outs, f32, as_float ? plane : -1);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     return cuda_err(cudaGetLastError());
 }
@@ -495,7 +541,7 @@ int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_
     uint8_t *m = s->mask[s->mask_parity];
     uint8_t *other = s->mask[s->mask_parity ^ 1];
     launch_footprint(g, v, m, s->counters, s->cs);
-    launch_select_tiles(g, m, other, s->tiles, s->counters, s->cs);
+    launch_select_tiles(g, m, other, s->tiles, s->cflags, s->counters, s->cs);
     s->mask_parity ^= 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mask_host)
@@ -557,7 +603,16 @@ int wv_profile_end(wv_stream *s, wv_profile *out) {
     return WV_OK;
 }
 
-int wv_launches_per_viewport(void) { return kLaunchesPerViewport; }
+int wv_launches_per_viewport(const wv_stream *s) {
+    if (!s) return WV_ERR_ARG;
+    return split_mode(s) ? 5 : 4;
+}
+
+int wv_set_decode_mode(wv_stream *s, int mode) {
+    if (!s || mode < 0 || mode > 1) return WV_ERR_ARG;
+    s->decode_mode = mode;
+    return WV_OK;
+}
 
 int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes, size_t *max_stream_bytes) {
     if (!desc) return WV_ERR_ARG;

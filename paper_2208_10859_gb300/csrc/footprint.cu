@@ -60,41 +60,71 @@ __global__ void k_footprint(View v, uint8_t *__restrict__ mask, int cells_x, int
 }
 
 // One thread per candidate tile of every plane: a tile is selected when any
-// mask cell it covers is set.  The other mask buffer (used by the next
-// viewport) is cleared on the way.
+// mask cell it covers is set.  A selected tile also flags the coarse tiles
+// (kCoarseTile samples of LL_2 per axis) that hold its LL_2 window
+// [q t - 3, q t + q + 2] (q = kTile / 4; 9/7 halo, the 5/3 window is
+// narrower), including the window's symmetric extension at the plane edges.
+// The other mask buffer (used by the next viewport) is cleared on the way.
+__device__ __forceinline__ bool any_cell(const Geom &g, const uint8_t *mask, const PlaneGeom &pg,
+                                         int px0, int px1, int py0, int py1) {
+    px1 = min(px1, pg.w);
+    py1 = min(py1, pg.h);
+    const int s = pg.sub;
+    const int cx0 = px0 * s / kCell, cx1 = min((px1 * s - 1) / kCell, g.cells_x - 1);
+    const int cy0 = py0 * s / kCell, cy1 = min((py1 * s - 1) / kCell, g.cells_y - 1);
+    for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx)
+            if (mask[cy * g.cells_x + cx]) return true;
+    return false;
+}
+
+// Coarse tiles [c_lo, c_hi] holding LL_2 indices [lo, hi] of a subband of n2
+// samples after whole-sample symmetric extension (mirrors at 0 and n2 - 1,
+// one further sample toward the inside at the right end for safety).
+__device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, int &c_hi) {
+    int a = max(lo, 0), b = min(hi, n2 - 1);
+    if (lo < 0) b = max(b, min(-lo, n2 - 1));
+    if (hi > n2 - 1) a = min(a, max(2 * (n2 - 1) - hi, 0));
+    c_lo = a / kCoarseTile;
+    c_hi = b / kCoarseTile;
+}
+
 __global__ void k_select_tiles(Geom g, const uint8_t *__restrict__ mask,
                                uint8_t *__restrict__ other, uint32_t *__restrict__ tiles,
-                               int *counters) {
+                               uint8_t *__restrict__ cflags, int *counters) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int ncells = g.cells_x * g.cells_y;
     for (int c = tid; c < ncells; c += gridDim.x * blockDim.x) other[c] = 0;
     if (tid >= g.total_tiles) return;
-    int plane = 0, t = tid;
+    int plane = 0, t = tid, cbase = 0;
     while (plane < g.planes - 1 && t >= g.p[plane].tiles_x * g.p[plane].tiles_y) {
         t -= g.p[plane].tiles_x * g.p[plane].tiles_y;
+        cbase += g.p[plane].ctiles_x * g.p[plane].ctiles_y;
         ++plane;
     }
     const PlaneGeom &pg = g.p[plane];
     const int tx = t % pg.tiles_x, ty = t / pg.tiles_x;
-    const int s = pg.sub;
-    const int cx0 = tx * kTile * s / kCell;
-    const int cx1 = min(((tx + 1) * kTile * s - 1) / kCell, g.cells_x - 1);
-    const int cy0 = ty * kTile * s / kCell;
-    const int cy1 = min(((ty + 1) * kTile * s - 1) / kCell, g.cells_y - 1);
-    bool hit = false;
-    for (int cy = cy0; cy <= cy1 && !hit; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx)
-            if (mask[cy * g.cells_x + cx]) { hit = true; break; }
-    if (hit) {
-        const int pos = atomicAdd(&counters[0], 1);
-        tiles[pos] = ((uint32_t)plane << 28) | ((uint32_t)ty << 14) | (uint32_t)tx;
-    }
+    if (!any_cell(g, mask, pg, tx * kTile, (tx + 1) * kTile, ty * kTile, (ty + 1) * kTile)) return;
+    const int pos = atomicAdd(&counters[0], 1);
+    tiles[pos] = ((uint32_t)plane << 28) | ((uint32_t)ty << 14) | (uint32_t)tx;
+    if (pg.ctiles_x == 0) return;
+    int cx0, cx1, cy0, cy1;
+    const int q = kTile / 4;   // LL_2 samples per tile side
+    coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, cx0, cx1);
+    coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, cy0, cy1);
+    for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) cflags[cbase + cy * pg.ctiles_x + cx] = 1;
+}
+
+__global__ void k_fill(uint8_t *p, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 1;
 }
 
 __global__ void k_all_tiles(int plane, int tiles_x, int tiles_y, uint32_t *tiles,
-                            int *counters) {
+                            int *count) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) counters[0] = tiles_x * tiles_y;
+    if (t == 0) *count = tiles_x * tiles_y;
     if (t >= tiles_x * tiles_y) return;
     tiles[t] = ((uint32_t)plane << 28) | ((uint32_t)(t / tiles_x) << 14) | (uint32_t)(t % tiles_x);
 }
@@ -120,20 +150,25 @@ void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters
 }
 
 void launch_select_tiles(const Geom &g, const uint8_t *mask, uint8_t *mask_other,
-                         uint32_t *tiles, int *counters, cudaStream_t cs) {
-    const int n = g.total_tiles > g.cells_x * g.cells_y ? g.total_tiles : g.cells_x * g.cells_y;
+                         uint32_t *tiles, uint8_t *cflags, int *counters, cudaStream_t cs) {
     const int threads = 256;
-    int blocks = (g.total_tiles + threads - 1) / threads;
-    if (blocks < 1) blocks = 1;
-    (void)n;
-    k_select_tiles<<<blocks, threads, 0, cs>>>(g, mask, mask_other, tiles, counters);
+    const int blocks = (g.total_tiles + threads - 1) / threads;
+    k_select_tiles<<<blocks > 0 ? blocks : 1, threads, 0, cs>>>(g, mask, mask_other, tiles, cflags,
+                                                                counters);
 }
 
 void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
                       cudaStream_t cs) {
     const int n = g.p[plane].tiles_x * g.p[plane].tiles_y;
     k_all_tiles<<<(n + 255) / 256, 256, 0, cs>>>(plane, g.p[plane].tiles_x, g.p[plane].tiles_y,
-                                                 tiles, counters);
+                                                 tiles, &counters[0]);
+}
+
+void launch_all_ctiles(const Geom &g, int plane, uint8_t *cflags, cudaStream_t cs) {
+    int base = 0;
+    for (int p = 0; p < plane; ++p) base += g.p[p].ctiles_x * g.p[p].ctiles_y;
+    const int n = g.p[plane].ctiles_x * g.p[plane].ctiles_y;
+    if (n > 0) k_fill<<<(n + 255) / 256, 256, 0, cs>>>(cflags + base, n);
 }
 
 void launch_project(const View &v, float *uv, cudaStream_t cs) {

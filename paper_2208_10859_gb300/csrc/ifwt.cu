@@ -1,24 +1,35 @@
-// ifwt.cu -- fused per-tile decode: coefficient gather, dequantisation,
-// inverse inter-frame Haar and every level of the 2D inverse FWT in one pass.
+// ifwt.cu -- tile decode: coefficient gather, dequantisation, inverse
+// inter-frame Haar and the 2D inverse FWT over a range of levels in one pass.
 //
 // Method: Sec. 3.5 rebuilds the wavelet representation of a frame on the GPU
-// (the inverse inter-frame transform of Sec. 3.2 iterates over the uploaded
-// coefficients, adding log2(n) detail coefficients with sign -1 or +1) and
-// then runs the 2D iFWT only over the masked region (Sec. 3.1).
+// (the inverse inter-frame transform of Sec. 3.2 adds log2(n) detail
+// coefficients with sign -1 or +1 to the low band) and then runs the 2D iFWT
+// only over the masked region (Sec. 3.1).
 //
-// Design: one CTA decodes one output tile (kTile x kTile samples of one
-// plane).  Working from the coarsest level down, level l needs the
-// coefficients of window K_l = [floor(K_{l-1}.lo / 2) - H, floor(K_{l-1}.hi /
-// 2) + H] (H = 2 for 9/7, whose synthesis reads 3 resp. 4 interleaved samples
-// to each side, H = 1 for 5/3), with K_0 the tile.  The interleaved array of
-// level l (LL from the previous level, HL/LH/HH gathered from global memory)
-// lives in shared memory; rows are synthesised first, then columns, each line
-// by one thread with a streaming (pipelined) lifting that keeps the four
-// lifting stages in registers.  Positions outside the plane are filled by
-// whole-sample symmetric extension at every level.  The finest level writes
-// the tile straight to the plane buffer.  No tensor cores: lifting is not a
-// contraction.
+// One CTA decodes one output tile at level l_bot - 1 (l_bot = 1: samples).
+// Working from level l_top down, level l needs the coefficients of the window
+// K_l = [floor(K_{l-1}.lo / 2) - H, floor(K_{l-1}.hi / 2) + H] (H = 2 for 9/7,
+// whose synthesis reads 3 resp. 4 interleaved samples on each side of an even
+// resp. odd output; H = 1 for 5/3), where K_{l-1} is the range the level below
+// needs.  Per level:
+//   gather + rows: each lane owns 8 coefficient columns (16 interleaved
+//     columns) of one array row: one aligned 16-byte load per subband and
+//     temporal band, dequantisation and the inter-frame rebuild in registers,
+//     then the horizontal lifting steps in registers with one warp shuffle per
+//     step for the neighbour lane's edge value; results go to shared array A;
+//   columns: every thread streams one column segment of A through the
+//     vertical lifting steps (four pipelined stages in registers) and writes
+//     the next level's LL window (shared P), an LL plane or the final samples.
+// Positions outside the plane are filled by whole-sample symmetric extension
+// at every level (edge chunks take a per-coefficient path).  Outputs within
+// the synthesis support of an array edge are invalid and never used.  No
+// tensor cores: lifting is not a contraction.
 #include <math.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "wv_impl.h"
 
@@ -40,294 +51,795 @@ struct Traits;
 template <>
 struct Traits<0> {   // LeGall 5/3, reversible integer lifting
     using T = int;
-    static constexpr int H = 1;
+    static constexpr int H = 1;      // coefficient halo per level
+    static constexpr int V = 2;      // invalid outputs at each line end
 };
 template <>
 struct Traits<1> {   // CDF 9/7, float lifting
     using T = float;
     static constexpr int H = 2;
+    static constexpr int V = 4;
 };
 
-struct Win {
-    int lo, hi;
-};
-
-// Streaming 1D synthesis of an interleaved line p[0..n) (stride st).  Each
-// output is emitted once all of its inputs have been read, so it may
-// overwrite the line in place.  Outputs closer than the synthesis support to
-// the line ends are not valid (the window halo absorbs them).
-template <class Emit>
-__device__ __forceinline__ void synth_line(float *p, int st, int n, Emit emit) {
-    float po = p[st];
-    float y1p = 0.f, y2pp = 0.f, y3pp = 0.f;
-    for (int k = 0; k < n / 2; ++k) {
-        const float e = p[(2 * k) * st];
-        const float o = p[(2 * k + 1) * st];
-        const float y1k = fmaf(-kDelta, po + o, e);          // even: -delta step
-        const float y2m = fmaf(-kGamma, y1p + y1k, po);      // odd:  -gamma step
-        const float y3m = fmaf(-kBeta, y2pp + y2m, y1p);     // even: -beta step
-        const float y4m = fmaf(-kAlpha, y3pp + y3m, y2pp);   // odd:  -alpha step
-        if (k >= 2) {
-            emit(2 * k - 4, y3pp);
-            emit(2 * k - 3, y4m);
-        }
-        y3pp = y3m;
-        y2pp = y2m;
-        y1p = y1k;
-        po = o;
-    }
-}
-
-template <class Emit>
-__device__ __forceinline__ void synth_line(int *p, int st, int n, Emit emit) {
-    int po = p[st];
-    int y1p = 0;
-    for (int k = 0; k < n / 2; ++k) {
-        const int e = p[(2 * k) * st];
-        const int o = p[(2 * k + 1) * st];
-        const int y1k = e - ((po + o + 2) >> 2);    // x[2k]   = s[k] - floor((d[k-1]+d[k]+2)/4)
-        const int y2m = po + ((y1p + y1k) >> 1);    // x[2k-1] = d[k-1] + floor((x[2k-2]+x[2k])/2)
-        if (k >= 1) {
-            emit(2 * k - 2, y1p);
-            emit(2 * k - 1, y2m);
-        }
-        y1p = y1k;
-        po = o;
-    }
-}
-
-struct DecodeArgs {
+struct TileArgs {
     Geom g;
     const int16_t *payload;
     const int32_t *table;
     Bands bands;
-    uint8_t *out_u8[3];
-    float *out_f32;
+    int l_top, l_bot;        // levels synthesised: l_top down to l_bot
+    int tile;                // output tile side at level l_bot - 1
+    const float *ll_in[3];   // LL_{l_top} planes when l_top < levels
+    int ll_in_pitch[3];
+    uint8_t *out_u8[3];      // l_bot == 1: samples
+    float *out_f32;          // l_bot == 1: float samples of plane f32_plane
     int f32_plane;
-    const uint32_t *tiles;
-    const int *counters;
+    float *ll_out[3];        // l_bot > 1: LL_{l_bot - 1} planes
+    int ll_out_pitch[3];
+    const uint32_t *tiles;   // tile list (count entries) ...
+    const int *count;
+    uint8_t *flags;          // ... or every tile of every plane, those flagged
+    int dense_count;         // number of tiles the flags cover
     int *err;
-    int buf_floats[2];
-    // 9/7: dequantisation step times the synthesis band scaling folded over
-    // all levels.  Synthesis scales a low band by K and a high band by 1/K
-    // per axis at every level, the LL produced by level l + 1 included; with
-    // LL_L x K^(2L), HL_l and LH_l x K^(2(l-1)), HH_l x K^(2(l-2)) the output
-    // of level l carries K^(2(l-1)), which is exactly the factor the next
-    // finer level expects of its LL, and level 1 returns unscaled samples.
+    int a_floats, p_floats;
+    // 9/7: half the dequantisation step times the synthesis band scaling
+    // folded over all levels.  Synthesis scales a low band by K and a high
+    // band by 1/K per axis at every level, the LL produced by level l + 1
+    // included; with LL_L x K^(2L), HL_l and LH_l x K^(2(l-1)), HH_l x
+    // K^(2(l-2)) the output of level l carries K^(2(l-1)), exactly the factor
+    // the next finer level expects of its LL, and level 1 returns unscaled
+    // samples.  (The half: the midpoint reconstruction is computed as
+    // (2q + sign q) step / 2.)
     float scale[kMaxLevels + 1][4];
 };
 
-// Dequantised, temporally rebuilt coefficient (sub, level, kx, ky) of a plane.
-template <int WAV>
-__device__ __forceinline__ typename Traits<WAV>::T gather(const DecodeArgs &a, const PlaneGeom &pg,
-                                                          int level, int sub, int kx, int ky) {
+struct Range {
+    int lo, hi;
+};
+
+__device__ __host__ __forceinline__ int floor8(int x) { return x & ~7; }
+
+// Index of coefficient k of a subband of n coefficients after whole-sample
+// symmetric extension of the interleaved line (low band: even positions,
+// high band: odd positions).
+__device__ __forceinline__ int refl_sub(int k, int n, int high) {
+    return reflect_idx(2 * k + high, 2 * n) >> 1;
+}
+
+// ---- per-level geometry ----------------------------------------------------
+
+struct LevelGeo {
+    int l;
+    Range ky;            // coefficient rows of the window
+    int kx0, nch;        // first coefficient column (multiple of 8), 8-wide chunks
+    int rows;            // interleaved array rows = 2 |ky|
+    Range ox, oy;        // outputs of this level (level l-1 coordinates)
+    int ja4, sa;         // A column origin (array column, multiple of 16), stride (multiple of 16)
+    int nw, nh;          // subband size at level l
+};
+
+// Layout of the next level's LL window in P, written by level l's columns:
+// rows oy, columns from floor8(ox.lo), stride a multiple of 8.
+struct PLayout {
+    int col0, stride;
+};
+
+__device__ __host__ __forceinline__ PLayout p_layout(Range ox) {
+    PLayout p;
+    p.col0 = floor8(ox.lo);
+    p.stride = 8 * ((ox.hi + 1 - p.col0 + 7) >> 3);
+    return p;
+}
+
+template <int H>
+__device__ __forceinline__ LevelGeo make_level(int l, Range ox, Range oy, int pw, int ph) {
+    LevelGeo G;
+    G.l = l;
+    G.ox = ox;
+    G.oy = oy;
+    const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
+    G.ky = {(oy.lo >> 1) - H, (oy.hi >> 1) + H};
+    G.kx0 = floor8(kx.lo);
+    G.nch = (kx.hi + 1 - G.kx0 + 7) >> 3;
+    G.rows = 2 * (G.ky.hi - G.ky.lo + 1);
+    G.ja4 = (ox.lo - 2 * G.kx0) & ~15;
+    G.sa = ((ox.hi - 2 * G.kx0 + 1) - G.ja4 + 15) & ~15;
+    G.nw = pw >> l;
+    G.nh = ph >> l;
+    return G;
+}
+
+// ---- dequantisation + inter-frame rebuild of 8 coefficients ----------------
+
+__device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xffffu); }
+__device__ __forceinline__ int hi16(uint32_t w) { return (int)(int16_t)(w >> 16); }
+
+template <int NB>
+struct Raw {
+    uint4 q[2][NB];      // [even/odd columns][band]
+    bool have[2][NB];
+};
+
+template <int WAV, int NB>
+__device__ __forceinline__ void combine8(const TileArgs &a, const uint4 *q, const bool *have,
+                                         float s, typename Traits<WAV>::T out[8]) {
+    if constexpr (WAV == 1) {
+        float acc[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            // absent block, or 8 coefficients in the dead zone: contributes 0
+            if (!have[b] || (q[b].x | q[b].y | q[b].z | q[b].w) == 0) continue;
+            const uint32_t w[4] = {q[b].x, q[b].y, q[b].z, q[b].w};
+            const float sg = (b == 0 || a.bands.bit[b]) ? 1.f : -1.f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int v = (m & 1) ? hi16(w[m >> 1]) : lo16(w[m >> 1]);
+                // dead-zone reconstruction at the interval midpoint:
+                // sign(q) (|q| + 1/2) = (2q + sign(q)) / 2
+                const int t = 2 * v + min(max(v, -1), 1);
+                acc[m] = fmaf(sg, (float)t, acc[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) out[m] = acc[m] * s;
+    } else {
+        const int st = (int)a.g.step;
+        int v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (!have[b] || (q[b].x | q[b].y | q[b].z | q[b].w) == 0) continue;   // adds 0
+            const uint32_t w[4] = {q[b].x, q[b].y, q[b].z, q[b].w};
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int qq = (m & 1) ? hi16(w[m >> 1]) : lo16(w[m >> 1]);
+                const int c = qq == 0 ? 0 : (qq > 0 ? qq * st + (st >> 1) : qq * st - (st >> 1));
+                if (b == 0) {
+                    v[m] = c;
+                } else {   // S-transform inverse: a = L - floor(H/2), b = a + H
+                    const int lo = v[m] - (c >> 1);
+                    v[m] = a.bands.bit[b] ? lo + c : lo;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) out[m] = v[m];
+    }
+}
+
+// Dequantised, rebuilt coefficient (scalar path for edge chunks).
+template <int WAV, int NB>
+__device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, const PlaneGeom &pg,
+                                                         int level, int sub, int kx, int ky) {
     const Geom &g = a.g;
     const int lb = g.log2b, bm = g.block - 1;
     const int bid = pg.base[level][sub] + (ky >> lb) * pg.nbx[level] + (kx >> lb);
-    const int off = ((ky & bm) << lb) + (kx & bm);
+    const size_t off = (size_t)((ky & bm) << lb) + (kx & bm);
     const size_t bsz = (size_t)g.block * g.block;
-    if constexpr (WAV == 1) {
-        float acc = 0.f;
-        for (int b = 0; b < a.bands.n; ++b) {
-            const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-            float c = 0.f;
-            if (slot >= 0) {
-                const int q = __ldg(&a.payload[(size_t)slot * bsz + off]);
-                // dead-zone reconstruction at the interval midpoint
-                if (q != 0) c = (float)q + (q > 0 ? 0.5f : -0.5f);
-            }
-            acc = (b == 0) ? c : (a.bands.bit[b] ? acc + c : acc - c);
+    uint4 q[NB];
+    bool have[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+        have[b] = slot >= 0;
+        const int v = have[b] ? (int)__ldg(&a.payload[(size_t)slot * bsz + off]) : 0;
+        q[b] = make_uint4((uint32_t)(uint16_t)v, 0, 0, 0);
+    }
+    typename Traits<WAV>::T out[8];
+    combine8<WAV, NB>(a, q, have, a.scale[level][sub], out);
+    return out[0];
+}
+
+template <class T>
+__device__ __forceinline__ T from_bits(float f) {
+    return reinterpret_cast<const T &>(f);
+}
+template <class T>
+__device__ __forceinline__ float to_bits(T v) {
+    return reinterpret_cast<const float &>(v);
+}
+
+// Position of column j of a row of A.  The 16-byte groups of a row are
+// XOR-swizzled so that the four float4 stores of the 8 chunks a warp writes
+// into one row hit 8 different bank groups, while a column keeps one
+// position in every row (the vertical pass reads conflict-free).
+__device__ __forceinline__ int swz(int j) {
+    const int g = j >> 2;
+    return ((g ^ ((g >> 3) & 3)) << 2) | (j & 3);
+}
+
+// ---- gather + horizontal synthesis ------------------------------------------
+
+struct Task {
+    bool active;
+    int jy, c;           // array row, chunk
+    int ky, py;          // coefficient row (after extension), row parity
+    bool fast;           // chunk entirely inside the subband (no extension)
+};
+
+template <int WAV, int NB>
+__device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg, const LevelGeo &G,
+                                          const Task &t, Raw<NB> &r) {
+    const Geom &g = a.g;
+    const int lb = g.log2b, bm = g.block - 1;
+    const size_t bsz = (size_t)g.block * g.block;
+    const int kx = G.kx0 + 8 * t.c;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int sub = e ? (t.py ? 3 : 1) : (t.py ? 2 : 0);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            r.have[e][b] = false;
+            r.q[e][b] = make_uint4(0, 0, 0, 0);
         }
-        return acc * a.scale[level][sub];
-    } else {
-        const int s = (int)a.g.step;
-        int v = 0;
-        for (int b = 0; b < a.bands.n; ++b) {
+        if (!t.active || !t.fast || (sub == 0 && G.l < g.levels)) continue;
+        const int bid = pg.base[G.l][sub] + (t.ky >> lb) * pg.nbx[G.l] + (kx >> lb);
+        const size_t off = (size_t)((t.ky & bm) << lb) + (kx & bm);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
             const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-            int c = 0;
             if (slot >= 0) {
-                const int q = __ldg(&a.payload[(size_t)slot * bsz + off]);
-                if (q != 0) c = q > 0 ? q * s + (s >> 1) : q * s - (s >> 1);
-            }
-            if (b == 0) {
-                v = c;
-            } else {   // S-transform inverse: a = L - floor(H/2), b = a + H
-                const int lo = v - (c >> 1);
-                v = a.bands.bit[b] ? lo + c : lo;
+                r.have[e][b] = true;
+                r.q[e][b] = __ldg(reinterpret_cast<const uint4 *>(a.payload + (size_t)slot * bsz + off));
             }
         }
-        return v;
     }
 }
 
-template <int WAV>
-__global__ void __launch_bounds__(kThreads, 2) k_decode_tiles(DecodeArgs a) {
+template <int WAV, int NB>
+__device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &pg, int plane,
+                                            const LevelGeo &G, const Task &t, const Raw<NB> &r,
+                                            const float *P, int nch, float *A) {
     using T = typename Traits<WAV>::T;
-    constexpr int H = Traits<WAV>::H;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *buf[2] = {reinterpret_cast<T *>(smem_raw),
-                 reinterpret_cast<T *>(smem_raw) + a.buf_floats[0]};
-    const int count = *(volatile const int *)a.counters;
     const Geom &g = a.g;
-    const int L = g.levels;
+    T v[16];
+    const int kx = G.kx0 + 8 * t.c;
+    const int s_even = t.py ? 2 : 0;
+    const int s_odd = t.py ? 3 : 1;
+    if (t.active) {
+        T ev[8], od[8];
+        // odd columns: HL (even row) or HH (odd row)
+        if (t.fast) {
+            combine8<WAV, NB>(a, r.q[1], r.have[1], a.scale[G.l][s_odd], od);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                od[m] = coef1<WAV, NB>(a, pg, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
+        }
+        // even columns: LH (odd row) or LL (even row)
+        if (s_even == 2 || G.l == g.levels) {
+            if (t.fast) {
+                combine8<WAV, NB>(a, r.q[0], r.have[0], a.scale[G.l][s_even], ev);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    ev[m] = coef1<WAV, NB>(a, pg, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
+            }
+        } else if (G.l == a.l_top) {   // LL from a plane written by a coarser pass
+            const float *src = a.ll_in[plane] + (size_t)t.ky * a.ll_in_pitch[plane];
+            if (t.fast) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src + kx));
+                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src + kx + 4));
+                const float f[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(f[m]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(src[refl_sub(kx + m, G.nw, 0)]);
+            }
+        } else {                       // LL from the level above (shared P)
+            const int sp = 8 * G.nch;
+            const float *prow = P + (t.ky - G.ky.lo) * sp;
+            if (t.fast) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(prow + 8 * t.c);
+                const float4 x1 = *reinterpret_cast<const float4 *>(prow + 8 * t.c + 4);
+                const float f[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(f[m]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(prow[refl_sub(kx + m, G.nw, 0) - G.kx0]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            v[2 * m] = ev[m];
+            v[2 * m + 1] = od[m];
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = T(0);
+    }
+    // horizontal synthesis across the row's lanes (chunk c sits next to chunk
+    // c - 1 and c + 1); lanes at the row ends use their own values, which only
+    // affects the invalid columns at the array edges
+    const bool has_l = t.c > 0, has_r = t.c < nch - 1;
+    if constexpr (WAV == 1) {
+        float L = __shfl_up_sync(0xffffffffu, v[15], 1);
+        if (!has_l) L = v[1];
+        v[0] = fmaf(-kDelta, L + v[1], v[0]);
+#pragma unroll
+        for (int m = 1; m < 8; ++m) v[2 * m] = fmaf(-kDelta, v[2 * m - 1] + v[2 * m + 1], v[2 * m]);
+        float R = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (!has_r) R = v[14];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) v[2 * m + 1] = fmaf(-kGamma, v[2 * m] + v[2 * m + 2], v[2 * m + 1]);
+        v[15] = fmaf(-kGamma, v[14] + R, v[15]);
+        L = __shfl_up_sync(0xffffffffu, v[15], 1);
+        if (!has_l) L = v[1];
+        v[0] = fmaf(-kBeta, L + v[1], v[0]);
+#pragma unroll
+        for (int m = 1; m < 8; ++m) v[2 * m] = fmaf(-kBeta, v[2 * m - 1] + v[2 * m + 1], v[2 * m]);
+        R = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (!has_r) R = v[14];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) v[2 * m + 1] = fmaf(-kAlpha, v[2 * m] + v[2 * m + 2], v[2 * m + 1]);
+        v[15] = fmaf(-kAlpha, v[14] + R, v[15]);
+    } else {
+        int L = __shfl_up_sync(0xffffffffu, v[15], 1);
+        if (!has_l) L = v[1];
+        v[0] -= (L + v[1] + 2) >> 2;
+#pragma unroll
+        for (int m = 1; m < 8; ++m) v[2 * m] -= (v[2 * m - 1] + v[2 * m + 1] + 2) >> 2;
+        int R = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (!has_r) R = v[14];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) v[2 * m + 1] += (v[2 * m] + v[2 * m + 2]) >> 1;
+        v[15] += (v[14] + R) >> 1;
+    }
+    if (!t.active) return;
+    // store the columns the vertical pass reads: A[jy][swz(j - ja4)]
+    const int j0 = 16 * t.c - G.ja4;
+    float *row = A + t.jy * G.sa;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + 4 * q;
+        if (j >= 0 && j + 4 <= G.sa) {
+            float4 w;
+            w.x = to_bits<T>(v[4 * q]);
+            w.y = to_bits<T>(v[4 * q + 1]);
+            w.z = to_bits<T>(v[4 * q + 2]);
+            w.w = to_bits<T>(v[4 * q + 3]);
+            *reinterpret_cast<float4 *>(row + swz(j)) = w;
+        }
+    }
+}
+
+template <int WAV, int NB>
+__device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &pg, int plane, const LevelGeo &G,
+                            const float *P, float *A) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nch = G.nch;
+    const int rpw = 32 / nch;               // rows per warp pass
+    const int r_in = lane / nch;            // row of this lane within the pass
+    const int c = lane - r_in * nch;        // chunk of this lane
+    const bool lane_ok = r_in < rpw;
+    const int stride = nwarps * rpw;
+    const int kxc = G.kx0 + 8 * c;
+    const bool fast_x = kxc >= 0 && kxc + 8 <= G.nw;
+    auto make = [&](int jy) {
+        Task t;
+        t.jy = jy;
+        t.c = c;
+        t.active = lane_ok && jy < G.rows;
+        int ry = t.active ? 2 * G.ky.lo + jy : 0;
+        if (ry < 0 || ry >= 2 * G.nh) ry = reflect_idx(ry, 2 * G.nh);
+        t.py = ry & 1;
+        t.ky = ry >> 1;
+        t.fast = fast_x;
+        return t;
+    };
+    for (int base = warp * rpw; base < G.rows; base += 2 * stride) {
+        const Task t0 = make(base + r_in);
+        const Task t1 = make(base + stride + r_in);
+        Raw<NB> r0, r1;
+        load_task<WAV, NB>(a, pg, G, t0, r0);
+        load_task<WAV, NB>(a, pg, G, t1, r1);
+        finish_task<WAV, NB>(a, pg, plane, G, t0, r0, P, nch, A);
+        finish_task<WAV, NB>(a, pg, plane, G, t1, r1, P, nch, A);
+    }
+}
+
+// ---- L2 prefetch of a tile's coefficient windows ---------------------------
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Issue bulk L2 prefetches for the stored coefficient rows (every subband
+// and temporal band, window rows clipped to the subband, 16-byte aligned
+// segments split at block boundaries) that the tile `e` reads, so that its
+// gathers find them in L2 when the CTA gets to it.
+template <int H>
+__device__ __forceinline__ void prefetch_tile(const TileArgs &a, int plane, int tx, int ty) {
+    const Geom &g = a.g;
+    const PlaneGeom &pg = g.p[plane];
+    const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
+    Range ox = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
+    Range oy = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
+    const int B = g.block, lb = g.log2b;
+    const size_t bsz = (size_t)B * B;
+    for (int l = a.l_bot; l <= a.l_top; ++l) {
+        const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
+        const Range ky = {(oy.lo >> 1) - H, (oy.hi >> 1) + H};
+        const int nw = pg.w >> l, nh = pg.h >> l;
+        const int x0 = max(floor8(kx.lo), 0), x1 = min((kx.hi + 8) & ~7, nw);   // [x0, x1)
+        const int y0 = max(ky.lo, 0), y1 = min(ky.hi, nh - 1);
+        const int nsub = (l == g.levels) ? 4 : 3;
+        const int nrows = y1 - y0 + 1;
+        const int work = nsub * a.bands.n * nrows;
+        for (int w = threadIdx.x; w < work && x1 > x0; w += blockDim.x) {
+            const int r = w % nrows, rest = w / nrows;
+            const int b = rest % a.bands.n, si = rest / a.bands.n;
+            const int sub = (nsub == 4) ? si : si + 1;
+            const int ky1 = y0 + r;
+            for (int xs = x0; xs < x1;) {
+                const int xe = min(x1, ((xs >> lb) + 1) << lb);   // end of this block
+                const int bid = pg.base[l][sub] + (ky1 >> lb) * pg.nbx[l] + (xs >> lb);
+                const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+                if (slot >= 0) {
+                    const int16_t *p = a.payload + (size_t)slot * bsz +
+                                       ((size_t)(ky1 & (B - 1)) << lb) + (xs & (B - 1));
+                    prefetch_l2(p, (uint32_t)(xe - xs) * 2u);
+                }
+                xs = xe;
+            }
+        }
+        ox = kx;
+        oy = ky;
+    }
+}
+
+// ---- vertical synthesis -----------------------------------------------------
+
+// Streaming synthesis of one column of A: emits array rows [r_a, r_b) (all
+// valid), reading rows from r_a - V (rounded down to even) on.  Values travel
+// as float bits (int bits for 5/3).  `col` is the (swizzled) column position.
+template <int WAV, class Emit>
+__device__ __forceinline__ void column_segment(const float *A, int sa, int col, int rows, int r_a,
+                                               int r_b, Emit emit) {
+    constexpr int VV = Traits<WAV>::V;
+    int i = max(0, (r_a - VV) & ~1);
+    const float *p = A + col;
+    if constexpr (WAV == 1) {
+        // pair i (rows i, i + 1) completes rows i - 4 (even) and i - 3 (odd)
+        float po = p[(i + 1) * sa];
+        float y1p = 0.f, y2pp = 0.f, y3pp = 0.f, y4m = 0.f;
+        auto step = [&](int r) {
+            const float e = p[r * sa];
+            const float o = p[(r + 1) * sa];
+            const float y1k = fmaf(-kDelta, po + o, e);          // even: -delta step
+            const float y2m = fmaf(-kGamma, y1p + y1k, po);      // odd:  -gamma step
+            const float y3m = fmaf(-kBeta, y2pp + y2m, y1p);     // even: -beta step
+            y4m = fmaf(-kAlpha, y3pp + y3m, y2pp);               // odd:  -alpha step
+            const float out_even = y3pp;
+            y3pp = y3m;
+            y2pp = y2m;
+            y1p = y1k;
+            po = o;
+            return out_even;
+        };
+        for (; i < r_a + 3; i += 2) step(i);                 // warm-up: nothing valid yet
+        if (i == r_a + 3) {                                  // odd r_a: only row i - 3
+            step(i);
+            emit(i - 3, y4m);
+            i += 2;
+        }
+        for (; i <= r_b + 2; i += 2) {                        // rows i - 4 and i - 3
+            const float ev = step(i);
+            emit(i - 4, ev);
+            emit(i - 3, y4m);
+        }
+        if (i - 4 <= r_b - 1 && i + 1 < rows) emit(i - 4, step(i));   // odd r_b: last even row
+    } else {
+        const int *pi = reinterpret_cast<const int *>(p);
+        int po = pi[(i + 1) * sa];
+        int y1p = 0, y2m = 0;
+        auto step = [&](int r) {
+            const int e = pi[r * sa];
+            const int o = pi[(r + 1) * sa];
+            const int y1k = e - ((po + o + 2) >> 2);    // x[r]   = s - floor((d_l + d_r + 2)/4)
+            y2m = po + ((y1p + y1k) >> 1);              // x[r-1] = d + floor((x[r-2] + x[r])/2)
+            const int out_even = y1p;
+            y1p = y1k;
+            po = o;
+            return out_even;
+        };
+        // pair i completes rows i - 2 (even) and i - 1 (odd)
+        for (; i < r_a + 1; i += 2) step(i);
+        if (i == r_a + 1) {
+            step(i);
+            emit(i - 1, __int_as_float(y2m));
+            i += 2;
+        }
+        for (; i <= r_b; i += 2) {
+            const int ev = step(i);
+            emit(i - 2, __int_as_float(ev));
+            emit(i - 1, __int_as_float(y2m));
+        }
+        if (i - 2 <= r_b - 1 && i + 1 < rows) emit(i - 2, __int_as_float(step(i)));
+    }
+}
+
+template <int WAV, int NB>
+__global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
+    constexpr int H = Traits<WAV>::H;
+    extern __shared__ __align__(16) float smem[];
+    float *A = smem;
+    float *P = smem + a.a_floats;
+    const Geom &g = a.g;
+    int count;
+    if (a.flags) count = a.dense_count;
+    else count = *(volatile const int *)a.count;
 
     for (int ti = blockIdx.x; ti < count; ti += gridDim.x) {
-        const uint32_t e = a.tiles[ti];
-        const int plane = (int)(e >> 28);
-        const int ty = (int)((e >> 14) & 0x3fff), tx = (int)(e & 0x3fff);
+        int plane, tx, ty;
+        if (a.flags) {   // dense enumeration of coarse tiles: skip unflagged ones
+            if (!a.flags[ti]) continue;
+            plane = 0;
+            int t = ti;
+            while (plane < g.planes - 1 && t >= g.p[plane].ctiles_x * g.p[plane].ctiles_y) {
+                t -= g.p[plane].ctiles_x * g.p[plane].ctiles_y;
+                ++plane;
+            }
+            tx = t % g.p[plane].ctiles_x;
+            ty = t / g.p[plane].ctiles_x;
+        } else {
+            const uint32_t e = a.tiles[ti];
+            plane = (int)(e >> 28);
+            ty = (int)((e >> 14) & 0x3fff);
+            tx = (int)(e & 0x3fff);
+        }
         const PlaneGeom &pg = g.p[plane];
-        const int X0 = tx * kTile, X1 = min(X0 + kTile, pg.w);
-        const int Y0 = ty * kTile, Y1 = min(Y0 + kTile, pg.h);
-
-        Win wx[kMaxLevels + 1], wy[kMaxLevels + 1];
-        wx[0] = {X0, X1 - 1};
-        wy[0] = {Y0, Y1 - 1};
-        for (int l = 1; l <= L; ++l) {
-            wx[l] = {(wx[l - 1].lo >> 1) - H, (wx[l - 1].hi >> 1) + H};
-            wy[l] = {(wy[l - 1].lo >> 1) - H, (wy[l - 1].hi >> 1) + H};
+        // the CTA's next tile: start pulling its coefficients into L2
+        if (!a.flags && ti + (int)gridDim.x < count) {
+            const uint32_t en = a.tiles[ti + gridDim.x];
+            prefetch_tile<H>(a, (int)(en >> 28), (int)(en & 0x3fff), (int)((en >> 14) & 0x3fff));
         }
-
-        for (int l = L; l >= 1; --l) {
-            T *cur = buf[(L - l) & 1];
-            const T *prev = buf[(L - l + 1) & 1];
-            const int aw = 2 * (wx[l].hi - wx[l].lo + 1);
-            const int ah = 2 * (wy[l].hi - wy[l].lo + 1);
-            const int st = aw + 1;
-            const int nx = pg.w >> (l - 1), ny = pg.h >> (l - 1);   // level l-1 size
-            const int gx0 = 2 * wx[l].lo, gy0 = 2 * wy[l].lo;
-            int pst = 0, pgx0 = 0, pgy0 = 0, pah = 0;
-            if (l < L) {
-                pst = 2 * (wx[l + 1].hi - wx[l + 1].lo + 1) + 1;
-                pah = 2 * (wy[l + 1].hi - wy[l + 1].lo + 1);
-                pgx0 = 2 * wx[l + 1].lo;
-                pgy0 = 2 * wy[l + 1].lo;
+        const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
+        // output ranges of every level (level l - 1 coordinates), l_bot upward
+        Range ox[kMaxLevels + 2], oy[kMaxLevels + 2];
+        ox[a.l_bot] = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
+        oy[a.l_bot] = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
+        for (int l = a.l_bot + 1; l <= a.l_top; ++l) {
+            ox[l] = {(ox[l - 1].lo >> 1) - H, (ox[l - 1].hi >> 1) + H};
+            oy[l] = {(oy[l - 1].lo >> 1) - H, (oy[l - 1].hi >> 1) + H};
+        }
+        for (int l = a.l_top; l >= a.l_bot; --l) {
+            const LevelGeo G = make_level<H>(l, ox[l], oy[l], pg.w, pg.h);
+            const PLayout pn = p_layout(G.ox);   // next level's LL window in P
+            const bool fits = G.rows * G.sa <= a.a_floats && G.nch <= 32 &&
+                              (l == a.l_bot || (G.oy.hi - G.oy.lo + 1) * pn.stride <= a.p_floats);
+            if (!fits) {   // never taken for the sizes the launcher computed
+                if (threadIdx.x == 0) record_error(a.err, WV_ERR_DEVICE);
+                break;
             }
-            // 1. build the interleaved array of level l
-            for (int idx = threadIdx.x; idx < aw * ah; idx += blockDim.x) {
-                const int jy = idx / aw, jx = idx - jy * aw;
-                const int ry = reflect_idx(gy0 + jy, ny), rx = reflect_idx(gx0 + jx, nx);
-                const int ky = ry >> 1, kx = rx >> 1;
-                const int sub = (rx & 1) + 2 * (ry & 1);   // 0 LL, 1 HL, 2 LH, 3 HH
-                T val;
-                if (sub == 0 && l < L) {
-                    const int py = ky - pgy0, px = kx - pgx0;
-                    if (py < 0 || py >= pah || px < 0 || px >= pst - 1) {
-                        record_error(a.err, WV_ERR_DEVICE);
-                        val = T(0);
-                    } else {
-                        val = prev[py * pst + px];
-                    }
+            // 1. gather + horizontal synthesis into A
+            gather_rows<WAV, NB>(a, pg, plane, G, P, A);
+            __syncthreads();
+            // 2. vertical synthesis of the columns the outputs need
+            const int nv = G.ox.hi - G.ox.lo + 1;
+            const int r0 = G.oy.lo - 2 * G.ky.lo, r1 = G.oy.hi - 2 * G.ky.lo + 1;
+            const int jc0 = G.ox.lo - 2 * G.kx0 - G.ja4;   // A column of output ox.lo (unswizzled)
+            const int nseg = max(1, min((int)blockDim.x / nv, (r1 - r0) / 16));
+            const int items = nv * nseg;
+            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                const int jj = it % nv, sg = it / nv;
+                const int ra = r0 + (r1 - r0) * sg / nseg, rb = r0 + (r1 - r0) * (sg + 1) / nseg;
+                const int x = G.ox.lo + jj;
+                if (l > a.l_bot) {
+                    float *dst = P + (x - pn.col0);
+                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                        dst[(2 * G.ky.lo + i - G.oy.lo) * pn.stride] = v;
+                    });
+                } else if (a.l_bot > 1) {
+                    float *dst = a.ll_out[plane] + x;
+                    const int pitch = a.ll_out_pitch[plane];
+                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                        dst[(size_t)(2 * G.ky.lo + i) * pitch] = v;
+                    });
+                } else if (a.out_f32 && plane == a.f32_plane) {
+                    float *o = a.out_f32 + x;
+                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                        const float f = (WAV == 1) ? v : (float)__float_as_int(v);
+                        o[(size_t)(2 * G.ky.lo + i) * pg.w] = f + 128.0f;
+                    });
                 } else {
-                    val = gather<WAV>(a, pg, l, sub, kx, ky);
-                }
-                cur[jy * st + jx] = val;
-            }
-            __syncthreads();
-            // 2. horizontal synthesis, one row per thread, in place
-            for (int r = threadIdx.x; r < ah; r += blockDim.x) {
-                T *row = cur + r * st;
-                synth_line(row, 1, aw, [&](int i, T v) { row[i] = v; });
-            }
-            __syncthreads();
-            // 3. vertical synthesis, one column per thread
-            if (l > 1) {
-                for (int c = threadIdx.x; c < aw; c += blockDim.x) {
-                    T *col = cur + c;
-                    synth_line(col, st, ah, [&](int i, T v) { col[i * st] = v; });
-                }
-            } else {
-                const int c0 = X0 - gx0, c1 = X1 - gx0;   // valid output columns
-                const int r0 = Y0 - gy0, r1 = Y1 - gy0;
-                for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-                    T *col = cur + c;
-                    const int x = X0 + (c - c0);
-                    if (a.out_f32 && plane == a.f32_plane) {
-                        float *o = a.out_f32 + x;
-                        synth_line(col, st, ah, [&](int i, T v) {
-                            if (i >= r0 && i < r1) o[(size_t)(Y0 + i - r0) * pg.w] = (float)v + 128.0f;
-                        });
-                    } else {
-                        uint8_t *o = a.out_u8[plane] + x;
-                        synth_line(col, st, ah, [&](int i, T v) {
-                            if (i >= r0 && i < r1) {
-                                int p;
-                                if constexpr (WAV == 1) p = __float2int_rd(v + 128.5f);
-                                else p = v + 128;
-                                o[(size_t)(Y0 + i - r0) * pg.w] = (uint8_t)min(max(p, 0), 255);
-                            }
-                        });
-                    }
+                    uint8_t *o = a.out_u8[plane] + x;
+                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                        int p;
+                        if constexpr (WAV == 1) p = __float2int_rd(v + 128.5f);
+                        else p = __float_as_int(v) + 128;
+                        o[(size_t)(2 * G.ky.lo + i) * pg.w] = (uint8_t)min(max(p, 0), 255);
+                    });
                 }
             }
             __syncthreads();
         }
+        if (a.flags && threadIdx.x == 0) a.flags[ti] = 0;   // consumed
     }
 }
 
-// Largest interleaved array (rows x (cols + 1)) per buffer parity.
-void buffer_sizes(const Geom &g, int out[2]) {
-    const int H = g.wavelet == WV_WAVELET_97 ? 2 : 1;
-    out[0] = out[1] = 0;
-    Win w{0, kTile - 1};
-    for (int l = 1; l <= g.levels; ++l) {
-        w = {(w.lo >> 1) - H, (w.hi >> 1) + H};
-        const int n = 2 * (w.hi - w.lo + 1);
-        const int sz = n * (n + 1);
-        int &slot = out[(g.levels - l) & 1];
-        if (sz > slot) slot = sz;
+// Shared-memory needs (floats) of A and P for tiles of side `tile` at level
+// l_bot - 1 synthesised from l_top.  Window sizes depend on the tile origin
+// only modulo 2^(l_top - l_bot + 4) * tile, which the scan covers.
+void smem_needs(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats) {
+    const int H = wavelet == WV_WAVELET_97 ? 2 : 1;
+    int amax = 0, pmax = 0;
+    for (int origin = 0; origin < 64 * tile; origin += tile) {
+        Range outs[kMaxLevels + 2];
+        outs[l_bot] = {origin, origin + tile - 1};
+        for (int l = l_bot + 1; l <= l_top; ++l)
+            outs[l] = {(outs[l - 1].lo >> 1) - H, (outs[l - 1].hi >> 1) + H};
+        for (int l = l_bot; l <= l_top; ++l) {
+            const Range ox = outs[l];
+            const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
+            const int kx0 = floor8(kx.lo);
+            const int rows = 2 * (kx.hi - kx.lo + 1);
+            const int ja4 = (ox.lo - 2 * kx0) & ~15;
+            const int sa = ((ox.hi - 2 * kx0 + 1) - ja4 + 15) & ~15;
+            if (rows * sa > amax) amax = rows * sa;
+            if (l > l_bot) {
+                const PLayout pn = p_layout(ox);
+                const int p = (ox.hi - ox.lo + 1) * pn.stride;
+                if (p > pmax) pmax = p;
+            }
+        }
     }
+    *a_floats = amax;
+    *p_floats = pmax;
+}
+
+std::mutex g_cache_mutex;
+
+void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats) {
+    static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> cache;
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    const auto key = std::make_tuple(wavelet, l_top, l_bot, tile);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        int af, pf;
+        smem_needs(wavelet, l_top, l_bot, tile, &af, &pf);
+        it = cache.emplace(key, std::make_pair(af, pf)).first;
+    }
+    *a_floats = it->second.first;
+    *p_floats = it->second.second;
+}
+
+template <int WAV, int NB>
+cudaError_t launch_t(const TileArgs &a, int grid, cudaStream_t cs) {
+    // largest dynamic shared memory opted in so far, per device
+    static int opted[64] = {};
+    const int smem = (a.a_floats + a.p_floats) * 4;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || smem > opted[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) opted[dev] = smem;
+    }
+    k_tiles<WAV, NB><<<grid, kThreads, smem, cs>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
+    smem_needs_cached(a.g.wavelet, a.l_top, a.l_bot, a.tile, &a.a_floats, &a.p_floats);
+    const double k2 = kK * kK;
+    for (int l = 0; l <= kMaxLevels; ++l) {
+        if (a.g.wavelet == WV_WAVELET_97) {
+            a.scale[l][0] = (float)(0.5 * a.g.step * pow(k2, a.g.levels));
+            a.scale[l][1] = a.scale[l][2] = (float)(0.5 * a.g.step * pow(k2, l - 1));
+            a.scale[l][3] = (float)(0.5 * a.g.step * pow(k2, l - 2));
+        } else {
+            a.scale[l][0] = a.scale[l][1] = a.scale[l][2] = a.scale[l][3] = 1.f;
+        }
+    }
+    const int grid = decode_tiles_grid(a.g);
+    const int nb = a.bands.n;
+    if (a.g.wavelet == WV_WAVELET_97) {
+        switch (nb) {
+        case 1: return launch_t<1, 1>(a, grid, cs);
+        case 2: return launch_t<1, 2>(a, grid, cs);
+        case 3: return launch_t<1, 3>(a, grid, cs);
+        default: return launch_t<1, 4>(a, grid, cs);
+        }
+    }
+    switch (nb) {
+    case 1: return launch_t<0, 1>(a, grid, cs);
+    case 2: return launch_t<0, 2>(a, grid, cs);
+    case 3: return launch_t<0, 3>(a, grid, cs);
+    default: return launch_t<0, 4>(a, grid, cs);
+    }
+}
+
+TileArgs base_args(const Geom &g, const int16_t *payload, const int32_t *table, const Bands &bands,
+                   int *err) {
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.payload = payload;
+    a.table = table;
+    a.bands = bands;
+    a.err = err;
+    a.f32_plane = -1;
+    return a;
 }
 
 }  // namespace
 
 int decode_tiles_smem_bytes(const Geom &g) {
-    int b[2];
-    buffer_sizes(g, b);
-    return (b[0] + b[1]) * 4;
+    int af, pf;
+    smem_needs(g.wavelet, g.levels, 1, kTile, &af, &pf);
+    return (af + pf) * 4;
 }
 
 int decode_tiles_grid(const Geom &g) {
+    (void)g;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms * 2;
 }
 
+// All levels of every listed tile in one kernel (no intermediate planes).
 cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int32_t *table,
                                 const Bands &bands, uint8_t *const *out_u8, float *out_f32,
                                 int f32_plane, const uint32_t *tiles, const int *counters,
                                 int *err, cudaStream_t cs) {
-    DecodeArgs a;
-    a.g = g;
-    a.payload = payload;
-    a.table = table;
-    a.bands = bands;
+    TileArgs a = base_args(g, payload, table, bands, err);
+    a.l_top = g.levels;
+    a.l_bot = 1;
+    a.tile = kTile;
     for (int p = 0; p < 3; ++p) a.out_u8[p] = out_u8[p];
     a.out_f32 = out_f32;
     a.f32_plane = f32_plane;
     a.tiles = tiles;
-    a.counters = counters;
-    a.err = err;
-    buffer_sizes(g, a.buf_floats);
-    const double k2 = kK * kK;
-    for (int l = 0; l <= kMaxLevels; ++l) {
-        a.scale[l][0] = (float)(g.step * pow(k2, g.levels));
-        a.scale[l][1] = a.scale[l][2] = (float)(g.step * pow(k2, l - 1));
-        a.scale[l][3] = (float)(g.step * pow(k2, l - 2));
+    a.count = counters;
+    return launch_args(a, cs);
+}
+
+// Coarse levels L..3 of the flagged coarse tiles (kCoarseTile x kCoarseTile
+// at level 2) into float LL_2 planes (float bits of int values for 5/3); the
+// flags are cleared as the tiles are done.
+cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
+                                 const Bands &bands, float *const *ll2, const int *ll2_pitch,
+                                 uint8_t *flags, int *err, cudaStream_t cs) {
+    TileArgs a = base_args(g, payload, table, bands, err);
+    a.l_top = g.levels;
+    a.l_bot = 3;
+    a.tile = kCoarseTile;
+    for (int p = 0; p < 3; ++p) {
+        a.ll_out[p] = ll2[p];
+        a.ll_out_pitch[p] = ll2_pitch[p];
     }
-    const int smem = (a.buf_floats[0] + a.buf_floats[1]) * 4;
-    const int grid = decode_tiles_grid(g);
-    cudaError_t e;
-    if (g.wavelet == WV_WAVELET_97) {
-        e = cudaFuncSetAttribute(k_decode_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        k_decode_tiles<1><<<grid, kThreads, smem, cs>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_decode_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        k_decode_tiles<0><<<grid, kThreads, smem, cs>>>(a);
+    a.flags = flags;
+    a.dense_count = g.total_ctiles;
+    return launch_args(a, cs);
+}
+
+// Levels 2 and 1 of the listed tiles, reading LL_2 from the planes written by
+// launch_decode_coarse.
+cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
+                               const Bands &bands, const float *const *ll2, const int *ll2_pitch,
+                               uint8_t *const *out_u8, float *out_f32, int f32_plane,
+                               const uint32_t *tiles, const int *count, int *err, cudaStream_t cs) {
+    TileArgs a = base_args(g, payload, table, bands, err);
+    a.l_top = 2;
+    a.l_bot = 1;
+    a.tile = kTile;
+    for (int p = 0; p < 3; ++p) {
+        a.ll_in[p] = ll2[p];
+        a.ll_in_pitch[p] = ll2_pitch[p];
+        a.out_u8[p] = out_u8[p];
     }
-    return cudaGetLastError();
+    a.out_f32 = out_f32;
+    a.f32_plane = f32_plane;
+    a.tiles = tiles;
+    a.count = count;
+    return launch_args(a, cs);
 }
 
 }  // namespace wv

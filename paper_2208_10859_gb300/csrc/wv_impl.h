@@ -5,7 +5,11 @@
 //   table     int32 [num_frames][nbpf]  slot of each block, -1 = all zero
 //   recon     uint8 per plane, width x height, row-major (decoded region)
 //   mask      uint8 [2][cells_y][cells_x] low-resolution binary masks
+//   ll2       float per plane, (w/4 rounded up to 8) x h/4: LL_2 of the
+//             coarse pass (levels >= 3)
 //   tiles     uint32 [max_tiles]        selected output tiles
+//   cflags    uint8 [coarse tiles]      coarse tiles the selected tiles need
+//             (set by tile selection, cleared by the coarse pass)
 //   counters  int32 [16]                 [0] = tile count
 //   err       int32                      first device-side error code
 #pragma once
@@ -24,6 +28,7 @@ constexpr int kMaxBands = 4;    // 1 + tlevels, tlevels <= 3
 constexpr int kCell = 32;       // luma pixels per mask cell (256 cells at 8192)
 constexpr int kTile = 128;      // output tile side (plane pixels)
 constexpr int kThreads = 256;   // threads of the tile-decode CTA
+constexpr int kCoarseTile = 128; // coarse tile side at level 2 (512 plane pixels)
 
 // Subband index inside a level: 0 = LL (level L only), 1 = HL, 2 = LH, 3 = HH.
 struct PlaneGeom {
@@ -32,7 +37,9 @@ struct PlaneGeom {
     int nby[kMaxLevels + 1];
     int base[kMaxLevels + 1][4];       // first block id of (level, subband)
     int tiles_x, tiles_y;
+    int ctiles_x, ctiles_y;            // coarse tiles (kCoarseTile at level 2)
     int sub;                           // luma pixels per plane pixel (1 or 2)
+    int ll2_pitch;                     // floats per row of the LL_2 plane
 };
 
 struct Geom {
@@ -41,6 +48,7 @@ struct Geom {
     PlaneGeom p[3];
     int cells_x, cells_y;
     int total_tiles;
+    int total_ctiles;
 };
 
 // Coefficient frames that rebuild one frame (inverse inter-frame Haar):
@@ -82,15 +90,23 @@ View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w
 void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters,
                       cudaStream_t cs);
 void launch_select_tiles(const Geom &g, const uint8_t *mask, uint8_t *mask_other,
-                         uint32_t *tiles, int *counters, cudaStream_t cs);
+                         uint32_t *tiles, uint8_t *cflags, int *counters, cudaStream_t cs);
 void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
                       cudaStream_t cs);
+void launch_all_ctiles(const Geom &g, int plane, uint8_t *cflags, cudaStream_t cs);
 int decode_tiles_smem_bytes(const Geom &g);
 int decode_tiles_grid(const Geom &g);
 cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int32_t *table,
                                 const Bands &bands, uint8_t *const *out_u8, float *out_f32,
                                 int f32_plane, const uint32_t *tiles, const int *counters,
                                 int *err, cudaStream_t cs);
+cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
+                                 const Bands &bands, float *const *ll2, const int *ll2_pitch,
+                                 uint8_t *cflags, int *err, cudaStream_t cs);
+cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
+                               const Bands &bands, const float *const *ll2, const int *ll2_pitch,
+                               uint8_t *const *out_u8, float *out_f32, int f32_plane,
+                               const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs);
 void launch_project(const View &v, float *uv, cudaStream_t cs);
@@ -115,6 +131,10 @@ struct wv_stream {
     uint8_t *mask[2] = {nullptr, nullptr};
     int mask_parity = 0;
     uint32_t *tiles = nullptr;
+    uint8_t *cflags = nullptr;
+    float *ll2[3] = {nullptr, nullptr, nullptr};
+    int ll2_pitch[3] = {0, 0, 0};
+    int decode_mode = 0;   // 0: coarse pass + fine pass (levels >= 3), 1: all levels fused
     int *counters = nullptr;
     int *err = nullptr;
     uint64_t n_payload = 0;

@@ -52,7 +52,7 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int * 8), ("tiles", ctypes.c_int)]
 
 
-KERNEL_NAMES = ["footprint", "select_tiles", "decode_tiles", "resample"]
+KERNEL_NAMES = ["footprint", "select_tiles", "decode_coarse", "decode_fine", "resample"]
 
 _LIB = None
 
@@ -85,7 +85,8 @@ def _lib():
             "wv_cone_bytes": (c_int, [vp, c_int, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
             "wv_profile_begin": (c_int, [vp]),
             "wv_profile_end": (c_int, [vp, ctypes.POINTER(Profile)]),
-            "wv_launches_per_viewport": (c_int, []),
+            "wv_launches_per_viewport": (c_int, [vp]),
+            "wv_set_decode_mode": (c_int, [vp, c_int]),
             "wv_encode_sizes": (c_int, [ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size), ctypes.POINTER(c_size)]),
             "wv_encode": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, vp, c_size,
                                   ctypes.POINTER(c_size), vp]),
@@ -107,6 +108,7 @@ def exported_symbols() -> list[str]:
             "wv_close_stream", "wv_decode_viewport", "wv_decode_batch", "wv_decode_full",
             "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
+            "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static"]
 
 
@@ -208,6 +210,12 @@ class Stream:
                                     ctypes.byref(out)), "wv_cone_bytes")
         return out.value
 
+    def set_decode_mode(self, mode: int) -> None:
+        _check(_lib().wv_set_decode_mode(self._handle, mode), "wv_set_decode_mode")
+
+    def launches_per_viewport(self) -> int:
+        return _lib().wv_launches_per_viewport(self._handle)
+
     def profile_begin(self) -> None:
         _check(_lib().wv_profile_begin(self._handle), "wv_profile_begin")
 
@@ -246,10 +254,6 @@ def decode_batch(requests: list, cuda_stream=None) -> None:
         arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out))
     _check(_lib().wv_decode_batch(arr, len(requests), ctypes.c_void_p(_cuda_stream_handle(cuda_stream))),
            "wv_decode_batch")
-
-
-def launches_per_viewport() -> int:
-    return _lib().wv_launches_per_viewport()
 
 
 def encode(frames, desc: dict, cuda_stream=None) -> bytes:

@@ -93,5 +93,8 @@ def test_encode_sizes(lib):
     assert lib.wv_encode_sizes(ctypes.byref(d), ctypes.byref(scratch), ctypes.byref(cap)) == -1
 
 
-def test_launch_count(lib):
-    assert lib.wv_launches_per_viewport() == 4
+def test_null_stream_arguments_are_rejected(lib):
+    assert lib.wv_launches_per_viewport(None) == -1
+    assert lib.wv_set_decode_mode(None, 0) == -1
+    assert lib.wv_decode_viewport(None, 0, 0.0, 0.0, 1.0, None) == -1
+    assert lib.wv_stream_sync_status(None) == -1

@@ -88,3 +88,26 @@ def test_decode_full_into_internal_planes_and_bad_args():
     with pytest.raises(wv.WVError):
         s.decode_full(0, 3)
     assert s.sync_status() == 0
+
+
+@pytest.mark.parametrize("name", ["yuv53", "yuv97", "gray97_L6", "ragged97"])
+def test_coarse_fine_split_equals_fused(name):
+    """The two-pass organisation (coarse levels into LL_2 planes, then levels
+    2..1) and the single fused pass give the same planes: bit-exact for 5/3,
+    within the 9/7 float tolerance otherwise."""
+    _, p, _, _ = H.case(name)
+    s = _stream(name)
+    for f in (0, p.num_frames - 1):
+        for pl in range(p.planes):
+            s.set_decode_mode(0)
+            a = _decode(s, f, pl, True)
+            s.set_decode_mode(1)
+            b = _decode(s, f, pl, True)
+            if p.wavelet == 0:
+                np.testing.assert_array_equal(a, b)
+            else:
+                assert np.abs(a.astype(np.float64) - b).max() <= H.tol_97_levels()
+    assert s.launches_per_viewport() == 4
+    s.set_decode_mode(0)
+    assert s.launches_per_viewport() == (5 if p.levels >= 3 else 4)
+    assert s.sync_status() == 0
