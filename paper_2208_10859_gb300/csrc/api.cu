@@ -345,6 +345,19 @@ Bands frame_bands(const Geom &g, int frame) {
     return b;
 }
 
+Frustum make_frustum(const View &v) {
+    // camera-space normals of x <= T z, x >= -T z, y <= T z, y >= -T z
+    const double T = v.t, nrm = 1.0 / sqrt(1.0 + T * T);
+    const double m[4][3] = {{-nrm, 0.0, T * nrm}, {nrm, 0.0, T * nrm},
+                            {0.0, -nrm, T * nrm}, {0.0, nrm, T * nrm}};
+    Frustum f;
+    for (int k = 0; k < 4; ++k)
+        for (int i = 0; i < 3; ++i)
+            f.n[k][i] = (float)(v.r[3 * i + 0] * m[k][0] + v.r[3 * i + 1] * m[k][1] +
+                                v.r[3 * i + 2] * m[k][2]);
+    return f;
+}
+
 View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h) {
     const double cy = cos((double)yaw), sy = sin((double)yaw);
     const double cp = cos((double)pitch), sp = sin((double)pitch);

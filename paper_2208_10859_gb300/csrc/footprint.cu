@@ -4,59 +4,81 @@
 // Sec. 3.1: the region to reconstruct is defined on a low-resolution binary
 // mask (256x256 for an 8k frame, i.e. 32-pixel cells) that can take any
 // shape; Sec. 3.6: the mapping pass reads the reconstructed region, so the
-// mask must hold every sample the mapping reads.  Here every viewport pixel
-// is projected with the same arithmetic as the mapping kernel and the cells
-// of its bilinear taps (luma and centre-sited chroma) are marked.  A margin
-// of 1/64 pixel around each position makes the mask cover positions computed
-// in higher precision as well.
+// mask must hold every sample the mapping reads.
 #include "wv_impl.h"
 
 namespace wv {
 
 namespace {
 
-constexpr float kMargin = 1.0f / 64.0f;
 
-// Mark the cells of the bilinear taps of every position within +-mu (x) and
-// +-mv (y) pixels of (u, v): columns floor(u - mu) .. floor(u + mu) + 1
-// (wrapping), rows floor(v - mv) .. floor(v + mv) + 1 (clamped).
-__device__ __forceinline__ void mark_taps(uint8_t *mask, int cells_x, int cells_y, float u,
-                                          float v, float mu, float mv, int w, int h, int cell) {
-    const int x_lo = (int)floorf(u - mu);
-    const int x_hi = (int)floorf(u + mu) + 1;
-    const int y_lo = min(max((int)floorf(v - mv), 0), h - 1);
-    const int y_hi = min(max((int)floorf(v + mv) + 1, 0), h - 1);
-    int c_lo = (x_lo >= 0 ? x_lo : x_lo - cell + 1) / cell;   // floor division
-    int c_hi = (x_hi >= 0 ? x_hi : x_hi - cell + 1) / cell;
-    if (c_hi - c_lo + 1 >= cells_x) {
-        c_lo = 0;
-        c_hi = cells_x - 1;
-    }
-    for (int cy = y_lo / cell; cy <= y_hi / cell && cy < cells_y; ++cy)
-        for (int c = c_lo; c <= c_hi; ++c) {
-            int cx = c % cells_x;
-            if (cx < 0) cx += cells_x;
-            mask[cy * cells_x + cx] = 1;
+// One thread per mask cell.  The viewport samples the frame at positions
+// inside the image of its frustum; every bilinear tap (luma, and centre-sited
+// chroma mapped to luma) lies within 2.5 luma pixels of its position.  A cell
+// is therefore needed when the cell grown by kReach pixels on every side
+// meets the frustum.  The grown cell is a longitude/latitude rectangle on the
+// sphere; it lies inside the spherical cap around its centre direction whose
+// angular radius rho is the largest angle to a corner (along a parallel or a
+// meridian the angle to a fixed point has at most one interior minimum, so
+// the farthest point is a corner).  The cap is tested against each of the
+// four frustum side planes (inward unit normals n_k): it meets half-space k
+// iff n_k . c >= -sin(rho).  Passing all four tests is necessary for meeting
+// the frustum, so the mask is a superset of the needed cells (cells near the
+// frustum's corners may be included without being needed).  Rows 0 and
+// H/32 - 1 extend to the poles because the resampler clamps v to the frame.
+constexpr float kReach = 3.0f;
+
+__global__ void k_footprint(View v, Frustum f, uint8_t *__restrict__ mask, int cells_x,
+                            int cells_y, int eq_w, int eq_h, int *counters) {
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx == 0 && cy == 0) counters[0] = 0;   // tile count of this viewport
+    if (cx >= cells_x || cy >= cells_y) return;
+    // grown cell in pixel coordinates -> longitude / latitude (radians / pi)
+    const float u0 = (float)(cx * kCell) - kReach, u1 = (float)((cx + 1) * kCell) + kReach;
+    const float v0 = (float)(cy * kCell) - kReach, v1 = (float)((cy + 1) * kCell) + kReach;
+    const float sx = 2.0f / (float)eq_w, sy = 1.0f / (float)eq_h;
+    const float lon0 = fmaf(u0 + 0.5f, sx, -1.0f), lon1 = fmaf(u1 + 0.5f, sx, -1.0f);
+    float lat0 = fmaf(-(v1 + 0.5f), sy, 0.5f), lat1 = fmaf(-(v0 + 0.5f), sy, 0.5f);
+    if (cy == 0) lat1 = 0.5f;
+    if (cy == cells_y - 1) lat0 = -0.5f;
+    lat0 = fmaxf(lat0, -0.5f);
+    lat1 = fminf(lat1, 0.5f);
+    const float lonc = 0.5f * (lon0 + lon1), latc = 0.5f * (lat0 + lat1);
+    // unit directions (x = cos lat sin lon, y = sin lat, z = cos lat cos lon)
+    float sa, ca, sb, cb, sc, cc, sl0, cl0, sl1, cl1, slc, clc;
+    sincospif(lat0, &sa, &ca);
+    sincospif(lat1, &sb, &cb);
+    sincospif(latc, &sc, &cc);
+    sincospif(lon0, &sl0, &cl0);
+    sincospif(lon1, &sl1, &cl1);
+    sincospif(lonc, &slc, &clc);
+    const float c[3] = {cc * slc, sc, cc * clc};
+    // smallest cosine to the four corners
+    float mincos = 1.0f;
+    const float cl[2] = {cl0, cl1}, sl[2] = {sl0, sl1};
+    const float clat[2] = {ca, cb}, slat[2] = {sa, sb};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float d = c[0] * clat[j] * sl[i] + c[1] * slat[j] + c[2] * clat[j] * cl[i];
+            mincos = fminf(mincos, d);
         }
-}
-
-__global__ void k_footprint(View v, uint8_t *__restrict__ mask, int cells_x, int cells_y,
-                            int eq_w, int eq_h, int chroma, int *counters) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i == 0 && j == 0) counters[0] = 0;   // tile count of this viewport
-    if (i >= v.out_w || j >= v.out_h) return;
-    float u, w, hxz;
-    project_px(v, i, j, u, w, &hxz);
-    // longitude error bound grows as 1 / cos(latitude) toward the poles
-    const float mu = fminf(kMargin + v.ku * 4e-6f / fmaxf(hxz, 1e-12f), (float)eq_w);
-    mark_taps(mask, cells_x, cells_y, u, w, mu, kMargin, eq_w, eq_h, kCell);
-    if (chroma) {
-        const float uc = fmaf(u + 0.5f, 0.5f, -0.5f);
-        const float vc = fmaf(w + 0.5f, 0.5f, -0.5f);
-        mark_taps(mask, cells_x, cells_y, uc, vc, 0.5f * mu, 0.5f * kMargin, eq_w / 2, eq_h / 2,
-                  kCell / 2);
+    mincos = fminf(fmaxf(mincos, -1.0f), 1.0f);
+    // sin(rho), with slack for float rounding of the dot products
+    const float srho = sqrtf(fmaxf(0.0f, 1.0f - mincos * mincos)) * 1.01f + 1e-5f;
+    bool hit = mincos > -0.5f;   // caps wider than 120 degrees: always keep
+    if (hit) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float d = f.n[k][0] * c[0] + f.n[k][1] * c[1] + f.n[k][2] * c[2];
+            hit = hit && (d >= -srho);
+        }
+    } else {
+        hit = true;
     }
+    mask[cy * cells_x + cx] = hit ? 1 : 0;
 }
 
 // One thread per candidate tile of every plane: a tile is selected when any
@@ -64,7 +86,6 @@ __global__ void k_footprint(View v, uint8_t *__restrict__ mask, int cells_x, int
 // (kCoarseTile samples of LL_2 per axis) that hold its LL_2 window
 // [q t - 3, q t + q + 2] (q = kTile / 4; 9/7 halo, the 5/3 window is
 // narrower), including the window's symmetric extension at the plane edges.
-// The other mask buffer (used by the next viewport) is cleared on the way.
 __device__ __forceinline__ bool any_cell(const Geom &g, const uint8_t *mask, const PlaneGeom &pg,
                                          int px0, int px1, int py0, int py1) {
     px1 = min(px1, pg.w);
@@ -93,8 +114,7 @@ __global__ void k_select_tiles(Geom g, const uint8_t *__restrict__ mask,
                                uint8_t *__restrict__ other, uint32_t *__restrict__ tiles,
                                uint8_t *__restrict__ cflags, int *counters) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncells = g.cells_x * g.cells_y;
-    for (int c = tid; c < ncells; c += gridDim.x * blockDim.x) other[c] = 0;
+    (void)other;
     if (tid >= g.total_tiles) return;
     int plane = 0, t = tid, cbase = 0;
     while (plane < g.planes - 1 && t >= g.p[plane].tiles_x * g.p[plane].tiles_y) {
@@ -143,10 +163,11 @@ __global__ void k_project(View v, float *uv) {
 
 void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters,
                       cudaStream_t cs) {
+    const Frustum f = make_frustum(v);
     dim3 block(32, 8);
-    dim3 grid((v.out_w + 31) / 32, (v.out_h + 7) / 8);
-    k_footprint<<<grid, block, 0, cs>>>(v, mask, g.cells_x, g.cells_y, g.p[0].w, g.p[0].h,
-                                        g.planes == 3 && g.c420, counters);
+    dim3 grid((g.cells_x + 31) / 32, (g.cells_y + 7) / 8);
+    k_footprint<<<grid, block, 0, cs>>>(v, f, mask, g.cells_x, g.cells_y, g.p[0].w, g.p[0].h,
+                                        counters);
 }
 
 void launch_select_tiles(const Geom &g, const uint8_t *mask, uint8_t *mask_other,

@@ -710,7 +710,7 @@ void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_float
 }
 
 template <int WAV, int NB>
-cudaError_t launch_t(const TileArgs &a, int grid, cudaStream_t cs) {
+cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
     // largest dynamic shared memory opted in so far, per device
     static int opted[64] = {};
     const int smem = (a.a_floats + a.p_floats) * 4;
@@ -721,7 +721,7 @@ cudaError_t launch_t(const TileArgs &a, int grid, cudaStream_t cs) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) opted[dev] = smem;
     }
-    k_tiles<WAV, NB><<<grid, kThreads, smem, cs>>>(a);
+    k_tiles<WAV, NB><<<grid, threads, smem, cs>>>(a);
     return cudaGetLastError();
 }
 
@@ -737,21 +737,25 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
             a.scale[l][0] = a.scale[l][1] = a.scale[l][2] = a.scale[l][3] = 1.f;
         }
     }
-    const int grid = decode_tiles_grid(a.g);
+    // the coarse pass has few, small tiles: 4-warp CTAs, four per SM (its
+    // latency, not its work, sets its duration); tile passes: 8 warps, two
+    const bool coarse = a.flags != nullptr;
+    const int threads = coarse ? kThreads / 2 : kThreads;
+    const int grid = decode_tiles_grid(a.g) * (coarse ? 2 : 1);
     const int nb = a.bands.n;
     if (a.g.wavelet == WV_WAVELET_97) {
         switch (nb) {
-        case 1: return launch_t<1, 1>(a, grid, cs);
-        case 2: return launch_t<1, 2>(a, grid, cs);
-        case 3: return launch_t<1, 3>(a, grid, cs);
-        default: return launch_t<1, 4>(a, grid, cs);
+        case 1: return launch_t<1, 1>(a, grid, threads, cs);
+        case 2: return launch_t<1, 2>(a, grid, threads, cs);
+        case 3: return launch_t<1, 3>(a, grid, threads, cs);
+        default: return launch_t<1, 4>(a, grid, threads, cs);
         }
     }
     switch (nb) {
-    case 1: return launch_t<0, 1>(a, grid, cs);
-    case 2: return launch_t<0, 2>(a, grid, cs);
-    case 3: return launch_t<0, 3>(a, grid, cs);
-    default: return launch_t<0, 4>(a, grid, cs);
+    case 1: return launch_t<0, 1>(a, grid, threads, cs);
+    case 2: return launch_t<0, 2>(a, grid, threads, cs);
+    case 3: return launch_t<0, 3>(a, grid, threads, cs);
+    default: return launch_t<0, 4>(a, grid, threads, cs);
     }
 }
 

@@ -24,21 +24,30 @@ constexpr int kGCb = (int)(2.0 * kKb * (1.0 - kKb) / kKg * 65536.0 + 0.5);
 constexpr int kGCr = (int)(2.0 * kKr * (1.0 - kKr) / kKg * 65536.0 + 0.5);
 constexpr int kBCb = (int)(2.0 * (1.0 - kKb) * 65536.0 + 0.5);
 
+// Bilinear sample of an 8-bit plane (w x h, row-major) at (u, v): x wraps
+// (projected positions lie in [-1/2, w - 1/2), so one conditional add
+// suffices; other positions take a modulo), y clamps.
 __device__ __forceinline__ int bilinear_u8(const uint8_t *__restrict__ img, int w, int h,
                                            float u, float v) {
     int x0, fx, y0, fy;
     fixed_split(u, x0, fx);
     fixed_split(v, y0, fy);
-    int xa = x0 % w;
+    int xa = x0;
     if (xa < 0) xa += w;
+    else if (xa >= w) xa -= w;
+    if ((unsigned)xa >= (unsigned)w) {   // positions far outside (caller-given)
+        xa %= w;
+        if (xa < 0) xa += w;
+    }
     const int xb = (xa + 1 == w) ? 0 : xa + 1;
     const int ya = min(max(y0, 0), h - 1);
     const int yb = min(max(y0 + 1, 0), h - 1);
-    const int p00 = __ldg(img + (size_t)ya * w + xa), p01 = __ldg(img + (size_t)ya * w + xb);
-    const int p10 = __ldg(img + (size_t)yb * w + xa), p11 = __ldg(img + (size_t)yb * w + xb);
-    const int acc = (256 - fx) * (256 - fy) * p00 + fx * (256 - fy) * p01 +
-                    (256 - fx) * fy * p10 + fx * fy * p11;
-    return (acc + 32768) >> 16;
+    const uint8_t *ra = img + ya * w, *rb = img + yb * w;   // planes are < 2^31 bytes
+    const int p00 = __ldg(ra + xa), p01 = __ldg(ra + xb);
+    const int p10 = __ldg(rb + xa), p11 = __ldg(rb + xb);
+    const int wx1 = fx, wx0 = 256 - fx;
+    const int top = wx0 * p00 + wx1 * p01, bot = wx0 * p10 + wx1 * p11;
+    return ((256 - fy) * top + fy * bot + 32768) >> 16;
 }
 
 __device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {

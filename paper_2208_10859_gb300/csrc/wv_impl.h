@@ -26,9 +26,10 @@ namespace wv {
 constexpr int kMaxLevels = 6;
 constexpr int kMaxBands = 4;    // 1 + tlevels, tlevels <= 3
 constexpr int kCell = 32;       // luma pixels per mask cell (256 cells at 8192)
+constexpr int kLogCell = 5;
 constexpr int kTile = 128;      // output tile side (plane pixels)
 constexpr int kThreads = 256;   // threads of the tile-decode CTA
-constexpr int kCoarseTile = 128; // coarse tile side at level 2 (512 plane pixels)
+constexpr int kCoarseTile = 64; // coarse tile side at level 2 (256 plane pixels)
 
 // Subband index inside a level: 0 = LL (level L only), 1 = HL, 2 = LH, 3 = HH.
 struct PlaneGeom {
@@ -70,6 +71,12 @@ struct View {
     int out_w, out_h;
 };
 
+// Inward unit normals (world coordinates) of the viewport frustum's four
+// side planes: a direction d is inside when n_k . d >= 0 for every k.
+struct Frustum {
+    float n[4][3];
+};
+
 struct StreamHeader {
     char magic[4];
     uint32_t version, width, height, planes, c420, levels, wavelet, num_frames,
@@ -85,6 +92,7 @@ constexpr size_t kHeaderBytes = 128;
 int build_geom(const wv_stream_desc &d, Geom *g);
 Bands frame_bands(const Geom &g, int frame);
 View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h);
+Frustum make_frustum(const View &v);
 
 // kernel launchers
 void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters,
