@@ -33,6 +33,13 @@ enum Kernel { kKFootprint = 0, kKTiles = 1, kKCoarse = 2, kKFine = 3, kKResample
 
 bool split_mode(const wv_stream *s) { return s->decode_mode == 0 && s->g.levels >= 3; }
 
+// Generation stamp of the next viewport (0 is never used: the stamp arrays
+// start zeroed).
+uint32_t next_gen(wv_stream *s) {
+    s->gen = s->gen + 1 == 0 ? 1 : s->gen + 1;
+    return s->gen;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
@@ -68,7 +75,7 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
 }
 
 struct Layout {
-    size_t payload, table, recon[3], ll2[3], mask[2], tiles, cflags, counters, err, total;
+    size_t payload, table, recon[3], ll2[3], mask, tiles, ctiles, tile_gen, ctile_gen, counters, err, total;
 };
 
 Layout layout(const Geom &g, uint64_t n_payload) {
@@ -87,14 +94,16 @@ Layout layout(const Geom &g, uint64_t n_payload) {
         if (p < g.planes && g.levels >= 3)
             o = align256(o + (size_t)g.p[p].ll2_pitch * (g.p[p].h >> 2) * 4);
     }
-    for (int m = 0; m < 2; ++m) {
-        L.mask[m] = o;
-        o = align256(o + (size_t)g.cells_x * g.cells_y);
-    }
+    L.mask = o;
+    o = align256(o + (size_t)g.cells_x * g.cells_y);
     L.tiles = o;
     o = align256(o + (size_t)g.total_tiles * 4);
-    L.cflags = o;
-    o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1));
+    L.ctiles = o;
+    o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
+    L.tile_gen = o;
+    o = align256(o + (size_t)g.total_tiles * 4);
+    L.ctile_gen = o;
+    o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
     L.counters = o;
     o = align256(o + 64);
     L.err = o;
@@ -141,8 +150,8 @@ cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, flo
     cudaError_t e;
     if (split_mode(s)) {
         prof_begin(s, kKCoarse);
-        e = launch_decode_coarse(g, s->payload, s->table, b, s->ll2, s->ll2_pitch, s->cflags,
-                                 s->err, s->cs);
+        e = launch_decode_coarse(g, s->payload, s->table, b, s->ll2, s->ll2_pitch, s->ctiles,
+                                 s->counters + 1, s->err, s->cs);
         prof_end(s);
         if (e != cudaSuccess) return e;
         const float *ll2c[3] = {s->ll2[0], s->ll2[1], s->ll2[2]};
@@ -168,15 +177,14 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     const Geom &g = s->g;
     const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, g.p[0].h);
     const Bands b = frame_bands(g, frame);
-    uint8_t *m = s->mask[s->mask_parity];
-    uint8_t *other = s->mask[s->mask_parity ^ 1];
+    uint8_t *m = s->mask;
+    const uint32_t gen = next_gen(s);
     prof_begin(s, kKFootprint);
-    launch_footprint(g, v, m, s->counters, s->cs);
+    launch_footprint(g, v, m, s->tile_gen, gen, s->counters, s->cs);
     prof_end(s);
     prof_begin(s, kKTiles);
-    launch_select_tiles(g, m, other, s->tiles, s->cflags, s->counters, s->cs);
+    launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
     prof_end(s);
-    s->mask_parity ^= 1;
     cudaError_t e = run_decode(s, b, s->recon, nullptr, -1);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     prof_begin(s, kKResample);
@@ -452,10 +460,11 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     s->payload = (int16_t *)(base + L.payload);
     s->table = (int32_t *)(base + L.table);
     for (int p = 0; p < 3; ++p) s->recon[p] = p < s->g.planes ? (uint8_t *)(base + L.recon[p]) : nullptr;
-    s->mask[0] = (uint8_t *)(base + L.mask[0]);
-    s->mask[1] = (uint8_t *)(base + L.mask[1]);
+    s->mask = (uint8_t *)(base + L.mask);
     s->tiles = (uint32_t *)(base + L.tiles);
-    s->cflags = (uint8_t *)(base + L.cflags);
+    s->ctiles = (uint32_t *)(base + L.ctiles);
+    s->tile_gen = (uint32_t *)(base + L.tile_gen);
+    s->ctile_gen = (uint32_t *)(base + L.ctile_gen);
     for (int p = 0; p < 3; ++p) {
         const bool has = p < s->g.planes && s->g.levels >= 3;
         s->ll2[p] = has ? (float *)(base + L.ll2[p]) : nullptr;
@@ -471,9 +480,8 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     if (e == cudaSuccess && h.n_payload)
         e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
                             h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.mask[0] - L.recon[0], s->cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.mask[0], 0, L.tiles - L.mask[0], s->cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.counters, 0, L.total - L.counters, s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.tile_gen, 0, L.total - L.tile_gen, s->cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -531,7 +539,7 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
         else outs[plane] = (uint8_t *)dptr;
     }
     launch_all_tiles(g, plane, s->tiles, s->counters, s->cs);
-    if (split_mode(s)) launch_all_ctiles(g, plane, s->cflags, s->cs);
+    if (split_mode(s)) launch_all_ctiles(g, plane, s->ctiles, s->counters, s->cs);
     cudaError_t e = run_decode(s, frame_bands(g, frame), outs, f32, as_float ? plane : -1);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     return cuda_err(cudaGetLastError());
@@ -551,11 +559,10 @@ int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_
     if (!s || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f)) return WV_ERR_ARG;
     const Geom &g = s->g;
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
-    uint8_t *m = s->mask[s->mask_parity];
-    uint8_t *other = s->mask[s->mask_parity ^ 1];
-    launch_footprint(g, v, m, s->counters, s->cs);
-    launch_select_tiles(g, m, other, s->tiles, s->cflags, s->counters, s->cs);
-    s->mask_parity ^= 1;
+    uint8_t *m = s->mask;
+    const uint32_t gen = next_gen(s);
+    launch_footprint(g, v, m, s->tile_gen, gen, s->counters, s->cs);
+    launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mask_host)
         e = cudaMemcpyAsync(mask_host, m, (size_t)g.cells_x * g.cells_y, cudaMemcpyDeviceToHost, s->cs);

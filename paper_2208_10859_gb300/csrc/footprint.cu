@@ -28,11 +28,12 @@ namespace {
 // H/32 - 1 extend to the poles because the resampler clamps v to the frame.
 constexpr float kReach = 3.0f;
 
-__global__ void k_footprint(View v, Frustum f, uint8_t *__restrict__ mask, int cells_x,
-                            int cells_y, int eq_w, int eq_h, int *counters) {
+__global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mask,
+                            uint32_t *__restrict__ tile_gen, uint32_t gen, int *counters) {
+    const int cells_x = g.cells_x, cells_y = g.cells_y, eq_w = g.p[0].w, eq_h = g.p[0].h;
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
     const int cy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (cx == 0 && cy == 0) counters[0] = 0;   // tile count of this viewport
+    if (cx == 0 && cy == 0) counters[0] = counters[1] = 0;   // tile counts of this viewport
     if (cx >= cells_x || cy >= cells_y) return;
     // grown cell in pixel coordinates -> longitude / latitude (radians / pi)
     const float u0 = (float)(cx * kCell) - kReach, u1 = (float)((cx + 1) * kCell) + kReach;
@@ -79,29 +80,24 @@ __global__ void k_footprint(View v, Frustum f, uint8_t *__restrict__ mask, int c
         hit = true;
     }
     mask[cy * cells_x + cx] = hit ? 1 : 0;
+    if (hit) {   // stamp the tile of every plane that holds this cell
+        int base = 0;
+        for (int p = 0; p < g.planes; ++p) {
+            const PlaneGeom &pg = g.p[p];
+            const int sh = (pg.sub == 2) ? 3 : 2;   // cells per tile side: 4 (or 8 at half size)
+            tile_gen[base + (cy >> sh) * pg.tiles_x + (cx >> sh)] = gen;
+            base += pg.tiles_x * pg.tiles_y;
+        }
+    }
 }
 
-// One thread per candidate tile of every plane: a tile is selected when any
-// mask cell it covers is set.  A selected tile also flags the coarse tiles
-// (kCoarseTile samples of LL_2 per axis) that hold its LL_2 window
-// [q t - 3, q t + q + 2] (q = kTile / 4; 9/7 halo, the 5/3 window is
-// narrower), including the window's symmetric extension at the plane edges.
-__device__ __forceinline__ bool any_cell(const Geom &g, const uint8_t *mask, const PlaneGeom &pg,
-                                         int px0, int px1, int py0, int py1) {
-    px1 = min(px1, pg.w);
-    py1 = min(py1, pg.h);
-    const int s = pg.sub;
-    const int cx0 = px0 * s / kCell, cx1 = min((px1 * s - 1) / kCell, g.cells_x - 1);
-    const int cy0 = py0 * s / kCell, cy1 = min((py1 * s - 1) / kCell, g.cells_y - 1);
-    for (int cy = cy0; cy <= cy1; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx)
-            if (mask[cy * g.cells_x + cx]) return true;
-    return false;
-}
-
-// Coarse tiles [c_lo, c_hi] holding LL_2 indices [lo, hi] of a subband of n2
-// samples after whole-sample symmetric extension (mirrors at 0 and n2 - 1,
-// one further sample toward the inside at the right end for safety).
+// One thread per candidate tile of every plane: a tile is selected when the
+// footprint stamped it with this viewport's generation.  A selected tile also
+// needs the coarse tiles (kCoarseTile samples of LL_2 per axis) that hold its
+// LL_2 window [q t - 3, q t + q + 2] (q = kTile / 4; 9/7 halo, the 5/3 window
+// is narrower), including the window's symmetric extension at the plane
+// edges; the first tile to claim a coarse tile (atomic exchange of its
+// generation stamp) appends it to the coarse list.
 __device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, int &c_hi) {
     int a = max(lo, 0), b = min(hi, n2 - 1);
     if (lo < 0) b = max(b, min(-lo, n2 - 1));
@@ -110,12 +106,12 @@ __device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, i
     c_hi = b / kCoarseTile;
 }
 
-__global__ void k_select_tiles(Geom g, const uint8_t *__restrict__ mask,
-                               uint8_t *__restrict__ other, uint32_t *__restrict__ tiles,
-                               uint8_t *__restrict__ cflags, int *counters) {
+__global__ void k_select_tiles(Geom g, const uint32_t *__restrict__ tile_gen,
+                               uint32_t *__restrict__ ctile_gen, uint32_t gen,
+                               uint32_t *__restrict__ tiles, uint32_t *__restrict__ ctiles,
+                               int *counters) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    (void)other;
-    if (tid >= g.total_tiles) return;
+    if (tid >= g.total_tiles || tile_gen[tid] != gen) return;
     int plane = 0, t = tid, cbase = 0;
     while (plane < g.planes - 1 && t >= g.p[plane].tiles_x * g.p[plane].tiles_y) {
         t -= g.p[plane].tiles_x * g.p[plane].tiles_y;
@@ -124,7 +120,6 @@ __global__ void k_select_tiles(Geom g, const uint8_t *__restrict__ mask,
     }
     const PlaneGeom &pg = g.p[plane];
     const int tx = t % pg.tiles_x, ty = t / pg.tiles_x;
-    if (!any_cell(g, mask, pg, tx * kTile, (tx + 1) * kTile, ty * kTile, (ty + 1) * kTile)) return;
     const int pos = atomicAdd(&counters[0], 1);
     tiles[pos] = ((uint32_t)plane << 28) | ((uint32_t)ty << 14) | (uint32_t)tx;
     if (pg.ctiles_x == 0) return;
@@ -133,12 +128,11 @@ __global__ void k_select_tiles(Geom g, const uint8_t *__restrict__ mask,
     coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, cx0, cx1);
     coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, cy0, cy1);
     for (int cy = cy0; cy <= cy1; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx) cflags[cbase + cy * pg.ctiles_x + cx] = 1;
-}
-
-__global__ void k_fill(uint8_t *p, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = 1;
+        for (int cx = cx0; cx <= cx1; ++cx)
+            if (atomicExch(&ctile_gen[cbase + cy * pg.ctiles_x + cx], gen) != gen) {
+                const int cpos = atomicAdd(&counters[1], 1);
+                ctiles[cpos] = ((uint32_t)plane << 28) | ((uint32_t)cy << 14) | (uint32_t)cx;
+            }
 }
 
 __global__ void k_all_tiles(int plane, int tiles_x, int tiles_y, uint32_t *tiles,
@@ -161,21 +155,21 @@ __global__ void k_project(View v, float *uv) {
 
 }  // namespace
 
-void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters,
-                      cudaStream_t cs) {
+void launch_footprint(const Geom &g, const View &v, uint8_t *mask, uint32_t *tile_gen,
+                      uint32_t gen, int *counters, cudaStream_t cs) {
     const Frustum f = make_frustum(v);
     dim3 block(32, 8);
     dim3 grid((g.cells_x + 31) / 32, (g.cells_y + 7) / 8);
-    k_footprint<<<grid, block, 0, cs>>>(v, f, mask, g.cells_x, g.cells_y, g.p[0].w, g.p[0].h,
-                                        counters);
+    k_footprint<<<grid, block, 0, cs>>>(v, f, g, mask, tile_gen, gen, counters);
 }
 
-void launch_select_tiles(const Geom &g, const uint8_t *mask, uint8_t *mask_other,
-                         uint32_t *tiles, uint8_t *cflags, int *counters, cudaStream_t cs) {
+void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, uint32_t *ctile_gen,
+                         uint32_t gen, uint32_t *tiles, uint32_t *ctiles, int *counters,
+                         cudaStream_t cs) {
     const int threads = 256;
     const int blocks = (g.total_tiles + threads - 1) / threads;
-    k_select_tiles<<<blocks > 0 ? blocks : 1, threads, 0, cs>>>(g, mask, mask_other, tiles, cflags,
-                                                                counters);
+    k_select_tiles<<<blocks > 0 ? blocks : 1, threads, 0, cs>>>(g, tile_gen, ctile_gen, gen, tiles,
+                                                                ctiles, counters);
 }
 
 void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
@@ -185,11 +179,11 @@ void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
                                                  tiles, &counters[0]);
 }
 
-void launch_all_ctiles(const Geom &g, int plane, uint8_t *cflags, cudaStream_t cs) {
-    int base = 0;
-    for (int p = 0; p < plane; ++p) base += g.p[p].ctiles_x * g.p[p].ctiles_y;
+void launch_all_ctiles(const Geom &g, int plane, uint32_t *ctiles, int *counters,
+                       cudaStream_t cs) {
     const int n = g.p[plane].ctiles_x * g.p[plane].ctiles_y;
-    if (n > 0) k_fill<<<(n + 255) / 256, 256, 0, cs>>>(cflags + base, n);
+    k_all_tiles<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, cs>>>(
+        plane, g.p[plane].ctiles_x, g.p[plane].ctiles_y, ctiles, &counters[1]);
 }
 
 void launch_project(const View &v, float *uv, cudaStream_t cs) {

@@ -75,10 +75,8 @@ struct TileArgs {
     int f32_plane;
     float *ll_out[3];        // l_bot > 1: LL_{l_bot - 1} planes
     int ll_out_pitch[3];
-    const uint32_t *tiles;   // tile list (count entries) ...
+    const uint32_t *tiles;   // tile list (count entries)
     const int *count;
-    uint8_t *flags;          // ... or every tile of every plane, those flagged
-    int dense_count;         // number of tiles the flags cover
     int *err;
     int a_floats, p_floats;
     // 9/7: half the dequantisation step times the synthesis band scaling
@@ -443,56 +441,6 @@ __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &
     }
 }
 
-// ---- L2 prefetch of a tile's coefficient windows ---------------------------
-
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Issue bulk L2 prefetches for the stored coefficient rows (every subband
-// and temporal band, window rows clipped to the subband, 16-byte aligned
-// segments split at block boundaries) that the tile `e` reads, so that its
-// gathers find them in L2 when the CTA gets to it.
-template <int H>
-__device__ __forceinline__ void prefetch_tile(const TileArgs &a, int plane, int tx, int ty) {
-    const Geom &g = a.g;
-    const PlaneGeom &pg = g.p[plane];
-    const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
-    Range ox = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
-    Range oy = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
-    const int B = g.block, lb = g.log2b;
-    const size_t bsz = (size_t)B * B;
-    for (int l = a.l_bot; l <= a.l_top; ++l) {
-        const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
-        const Range ky = {(oy.lo >> 1) - H, (oy.hi >> 1) + H};
-        const int nw = pg.w >> l, nh = pg.h >> l;
-        const int x0 = max(floor8(kx.lo), 0), x1 = min((kx.hi + 8) & ~7, nw);   // [x0, x1)
-        const int y0 = max(ky.lo, 0), y1 = min(ky.hi, nh - 1);
-        const int nsub = (l == g.levels) ? 4 : 3;
-        const int nrows = y1 - y0 + 1;
-        const int work = nsub * a.bands.n * nrows;
-        for (int w = threadIdx.x; w < work && x1 > x0; w += blockDim.x) {
-            const int r = w % nrows, rest = w / nrows;
-            const int b = rest % a.bands.n, si = rest / a.bands.n;
-            const int sub = (nsub == 4) ? si : si + 1;
-            const int ky1 = y0 + r;
-            for (int xs = x0; xs < x1;) {
-                const int xe = min(x1, ((xs >> lb) + 1) << lb);   // end of this block
-                const int bid = pg.base[l][sub] + (ky1 >> lb) * pg.nbx[l] + (xs >> lb);
-                const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-                if (slot >= 0) {
-                    const int16_t *p = a.payload + (size_t)slot * bsz +
-                                       ((size_t)(ky1 & (B - 1)) << lb) + (xs & (B - 1));
-                    prefetch_l2(p, (uint32_t)(xe - xs) * 2u);
-                }
-                xs = xe;
-            }
-        }
-        ox = kx;
-        oy = ky;
-    }
-}
-
 // ---- vertical synthesis -----------------------------------------------------
 
 // Streaming synthesis of one column of A: emits array rows [r_a, r_b) (all
@@ -571,34 +519,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
     float *A = smem;
     float *P = smem + a.a_floats;
     const Geom &g = a.g;
-    int count;
-    if (a.flags) count = a.dense_count;
-    else count = *(volatile const int *)a.count;
+    const int count = *(volatile const int *)a.count;
 
     for (int ti = blockIdx.x; ti < count; ti += gridDim.x) {
-        int plane, tx, ty;
-        if (a.flags) {   // dense enumeration of coarse tiles: skip unflagged ones
-            if (!a.flags[ti]) continue;
-            plane = 0;
-            int t = ti;
-            while (plane < g.planes - 1 && t >= g.p[plane].ctiles_x * g.p[plane].ctiles_y) {
-                t -= g.p[plane].ctiles_x * g.p[plane].ctiles_y;
-                ++plane;
-            }
-            tx = t % g.p[plane].ctiles_x;
-            ty = t / g.p[plane].ctiles_x;
-        } else {
-            const uint32_t e = a.tiles[ti];
-            plane = (int)(e >> 28);
-            ty = (int)((e >> 14) & 0x3fff);
-            tx = (int)(e & 0x3fff);
-        }
+        const uint32_t e = a.tiles[ti];
+        const int plane = (int)(e >> 28);
+        const int ty = (int)((e >> 14) & 0x3fff), tx = (int)(e & 0x3fff);
         const PlaneGeom &pg = g.p[plane];
-        // the CTA's next tile: start pulling its coefficients into L2
-        if (!a.flags && ti + (int)gridDim.x < count) {
-            const uint32_t en = a.tiles[ti + gridDim.x];
-            prefetch_tile<H>(a, (int)(en >> 28), (int)(en & 0x3fff), (int)((en >> 14) & 0x3fff));
-        }
         const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
         // output ranges of every level (level l - 1 coordinates), l_bot upward
         Range ox[kMaxLevels + 2], oy[kMaxLevels + 2];
@@ -659,7 +586,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
             }
             __syncthreads();
         }
-        if (a.flags && threadIdx.x == 0) a.flags[ti] = 0;   // consumed
     }
 }
 
@@ -739,7 +665,7 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
     }
     // the coarse pass has few, small tiles: 4-warp CTAs, four per SM (its
     // latency, not its work, sets its duration); tile passes: 8 warps, two
-    const bool coarse = a.flags != nullptr;
+    const bool coarse = a.l_bot > 1;
     const int threads = coarse ? kThreads / 2 : kThreads;
     const int grid = decode_tiles_grid(a.g) * (coarse ? 2 : 1);
     const int nb = a.bands.n;
@@ -805,12 +731,11 @@ cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int
     return launch_args(a, cs);
 }
 
-// Coarse levels L..3 of the flagged coarse tiles (kCoarseTile x kCoarseTile
-// at level 2) into float LL_2 planes (float bits of int values for 5/3); the
-// flags are cleared as the tiles are done.
+// Coarse levels L..3 of the listed coarse tiles (kCoarseTile x kCoarseTile at
+// level 2) into float LL_2 planes (float bits of int values for 5/3).
 cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, float *const *ll2, const int *ll2_pitch,
-                                 uint8_t *flags, int *err, cudaStream_t cs) {
+                                 const uint32_t *tiles, const int *count, int *err, cudaStream_t cs) {
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = g.levels;
     a.l_bot = 3;
@@ -819,8 +744,8 @@ cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const in
         a.ll_out[p] = ll2[p];
         a.ll_out_pitch[p] = ll2_pitch[p];
     }
-    a.flags = flags;
-    a.dense_count = g.total_ctiles;
+    a.tiles = tiles;
+    a.count = count;
     return launch_args(a, cs);
 }
 

@@ -71,18 +71,7 @@ struct ResampleArgs {
     size_t pitch;
 };
 
-__global__ void k_resample(ResampleArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= a.v.out_w || j >= a.v.out_h) return;
-    float u, v;
-    if (a.uv) {
-        const float2 p = reinterpret_cast<const float2 *>(a.uv)[(size_t)j * a.v.out_w + i];
-        u = p.x;
-        v = p.y;
-    } else {
-        project_px(a.v, i, j, u, v);
-    }
+__device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, float v) {
     const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
     int cb = 128, cr = 128;
     if (a.planes == 3) {
@@ -94,7 +83,47 @@ __global__ void k_resample(ResampleArgs a) {
         cb = bilinear_u8(a.plane[1], a.w[1], a.h[1], uc, vc);
         cr = bilinear_u8(a.plane[2], a.w[2], a.h[2], uc, vc);
     }
-    reinterpret_cast<uchar4 *>(a.out + (size_t)j * a.pitch)[i] = to_rgba(y, cb, cr);
+    return to_rgba(y, cb, cr);
+}
+
+// Two horizontally adjacent pixels per thread (independent work for the
+// scheduler to overlap), written with one 8-byte store when aligned.
+__global__ void k_resample(ResampleArgs a) {
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.v.out_w || j >= a.v.out_h) return;
+    const bool two = i + 1 < a.v.out_w;
+    float u0, v0, u1 = 0.f, v1 = 0.f;
+    if (a.uv) {
+        const float2 *row = reinterpret_cast<const float2 *>(a.uv) + (size_t)j * a.v.out_w;
+        const float2 p0 = row[i];
+        u0 = p0.x;
+        v0 = p0.y;
+        if (two) {
+            const float2 p1 = row[i + 1];
+            u1 = p1.x;
+            v1 = p1.y;
+        }
+    } else {
+        project_px(a.v, i, j, u0, v0);
+        if (two) project_px(a.v, i + 1, j, u1, v1);
+    }
+    const uchar4 c0 = sample_px(a, u0, v0);
+    uchar4 *dst = reinterpret_cast<uchar4 *>(a.out + (size_t)j * a.pitch) + i;
+    if (two) {
+        const uchar4 c1 = sample_px(a, u1, v1);
+        if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+            uint2 w;
+            w.x = (uint32_t)c0.x | ((uint32_t)c0.y << 8) | ((uint32_t)c0.z << 16) | ((uint32_t)c0.w << 24);
+            w.y = (uint32_t)c1.x | ((uint32_t)c1.y << 8) | ((uint32_t)c1.z << 16) | ((uint32_t)c1.w << 24);
+            *reinterpret_cast<uint2 *>(dst) = w;
+        } else {
+            dst[0] = c0;
+            dst[1] = c1;
+        }
+    } else {
+        dst[0] = c0;
+    }
 }
 
 }  // namespace
@@ -114,7 +143,7 @@ void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const 
     a.out = out;
     a.pitch = pitch;
     dim3 block(32, 8);
-    dim3 grid((v.out_w + 31) / 32, (v.out_h + 7) / 8);
+    dim3 grid((v.out_w + 63) / 64, (v.out_h + 7) / 8);
     k_resample<<<grid, block, 0, cs>>>(a);
 }
 

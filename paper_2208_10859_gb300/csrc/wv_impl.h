@@ -4,13 +4,14 @@
 //   payload   int16 [n_payload][B][B]   stored coefficient blocks, row-major
 //   table     int32 [num_frames][nbpf]  slot of each block, -1 = all zero
 //   recon     uint8 per plane, width x height, row-major (decoded region)
-//   mask      uint8 [2][cells_y][cells_x] low-resolution binary masks
+//   mask      uint8 [cells_y][cells_x]  low-resolution binary mask
 //   ll2       float per plane, (w/4 rounded up to 8) x h/4: LL_2 of the
 //             coarse pass (levels >= 3)
 //   tiles     uint32 [max_tiles]        selected output tiles
-//   cflags    uint8 [coarse tiles]      coarse tiles the selected tiles need
-//             (set by tile selection, cleared by the coarse pass)
-//   counters  int32 [16]                 [0] = tile count
+//   tile_gen  uint32 [tiles]            generation that last selected a tile
+//   ctile_gen uint32 [coarse tiles]      generation that last listed a coarse tile
+//   ctiles    uint32 [coarse tiles]      coarse tiles the selected tiles need
+//   counters  int32 [16]                 [0] = tile count, [1] = coarse tile count
 //   err       int32                      first device-side error code
 #pragma once
 
@@ -95,13 +96,15 @@ View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w
 Frustum make_frustum(const View &v);
 
 // kernel launchers
-void launch_footprint(const Geom &g, const View &v, uint8_t *mask, int *counters,
-                      cudaStream_t cs);
-void launch_select_tiles(const Geom &g, const uint8_t *mask, uint8_t *mask_other,
-                         uint32_t *tiles, uint8_t *cflags, int *counters, cudaStream_t cs);
+void launch_footprint(const Geom &g, const View &v, uint8_t *mask, uint32_t *tile_gen,
+                      uint32_t gen, int *counters, cudaStream_t cs);
+void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, uint32_t *ctile_gen,
+                         uint32_t gen, uint32_t *tiles, uint32_t *ctiles, int *counters,
+                         cudaStream_t cs);
 void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
                       cudaStream_t cs);
-void launch_all_ctiles(const Geom &g, int plane, uint8_t *cflags, cudaStream_t cs);
+void launch_all_ctiles(const Geom &g, int plane, uint32_t *ctiles, int *counters,
+                       cudaStream_t cs);
 int decode_tiles_smem_bytes(const Geom &g);
 int decode_tiles_grid(const Geom &g);
 cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int32_t *table,
@@ -110,7 +113,7 @@ cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int
                                 int *err, cudaStream_t cs);
 cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, float *const *ll2, const int *ll2_pitch,
-                                 uint8_t *cflags, int *err, cudaStream_t cs);
+                                 const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
                                const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                uint8_t *const *out_u8, float *out_f32, int f32_plane,
@@ -136,10 +139,12 @@ struct wv_stream {
     int16_t *payload = nullptr;
     int32_t *table = nullptr;
     uint8_t *recon[3] = {nullptr, nullptr, nullptr};
-    uint8_t *mask[2] = {nullptr, nullptr};
-    int mask_parity = 0;
+    uint8_t *mask = nullptr;
     uint32_t *tiles = nullptr;
-    uint8_t *cflags = nullptr;
+    uint32_t *tile_gen = nullptr;
+    uint32_t *ctile_gen = nullptr;
+    uint32_t *ctiles = nullptr;
+    uint32_t gen = 0;   // viewport generation (stamps in tile_gen / ctile_gen)
     float *ll2[3] = {nullptr, nullptr, nullptr};
     int ll2_pitch[3] = {0, 0, 0};
     int decode_mode = 0;   // 0: coarse pass + fine pass (levels >= 3), 1: all levels fused
