@@ -145,9 +145,10 @@ def measured_peak_hbm():
 
 
 def traffic_record():
-    """dram bytes per decode_tiles launch from the committed ncu summary, if
-    it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "decode_tiles_traffic.json")
+    """DRAM traffic of the tile-decode passes from the committed ncu summary
+    (as a ratio to the captured launch's algorithmic bytes), if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_tiles_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -348,13 +349,16 @@ def run_ours(args):
             "roofline": {"kernel": "tile decode (k_tiles coarse + fine passes)", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None if trec is None else trec["traffic_bytes_per_launch"],
+                         "traffic": None if trec is None else trec["traffic_over_alg"] * alg_dec / len(poses),
+                         "traffic_note": None if trec is None else trec["note"],
                          "algorithmic_bytes_per_launch": alg_dec / len(poses),
                          "avg_launch_ms": dec_ms / max(1, dec_n)},
             "kernel_ms_per_launch": kernel_ms,
             "decode_ms_per_viewport": {"split (coarse + fine)": dec_ms / max(1, dec_n),
                                        "fused (all levels per tile)": fused_ms},
             "viewport_bytes": {"cone_coef_mean": sum(cone) / len(cone), "region_mean": sum(region) / len(region),
+                               "per_pose_decode_alg": ([c + r for c, r in zip(cone, region)]
+                                                       if len(poses) <= 8 else None),
                                "rgba": out_bytes,
                                "whole_path_alg_GBps": (sum(cone) + len(poses) * out_bytes) * args.steps / (ms / 1e3) / 1e9},
             "clocks": clk.summary(),

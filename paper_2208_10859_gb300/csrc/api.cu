@@ -180,7 +180,7 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     uint8_t *m = s->mask;
     const uint32_t gen = next_gen(s);
     prof_begin(s, kKFootprint);
-    launch_footprint(g, v, m, s->tile_gen, gen, s->counters, s->cs);
+    launch_footprint(g, v, m, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
     prof_end(s);
     prof_begin(s, kKTiles);
     launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
@@ -561,7 +561,7 @@ int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
     uint8_t *m = s->mask;
     const uint32_t gen = next_gen(s);
-    launch_footprint(g, v, m, s->tile_gen, gen, s->counters, s->cs);
+    launch_footprint(g, v, m, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
     launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mask_host)

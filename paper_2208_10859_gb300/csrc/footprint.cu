@@ -26,10 +26,23 @@ namespace {
 // the frustum, so the mask is a superset of the needed cells (cells near the
 // frustum's corners may be included without being needed).  Rows 0 and
 // H/32 - 1 extend to the poles because the resampler clamps v to the frame.
+// Coarse tiles [c_lo, c_hi] (kCoarseTile samples of LL_2) holding LL_2
+// indices [lo, hi] of a subband of n2 samples after whole-sample symmetric
+// extension.  A tile t needs the LL_2 window [q t - 3, q t + q + 2]
+// (q = kTile / 4; 9/7 halo, the 5/3 window is narrower).
+__device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, int &c_hi) {
+    int a = max(lo, 0), b = min(hi, n2 - 1);
+    if (lo < 0) b = max(b, min(-lo, n2 - 1));
+    if (hi > n2 - 1) a = min(a, max(2 * (n2 - 1) - hi, 0));
+    c_lo = a / kCoarseTile;
+    c_hi = b / kCoarseTile;
+}
+
 constexpr float kReach = 3.0f;
 
 __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mask,
-                            uint32_t *__restrict__ tile_gen, uint32_t gen, int *counters) {
+                            uint32_t *__restrict__ tile_gen, uint32_t *__restrict__ ctile_gen,
+                            uint32_t gen, int *counters) {
     const int cells_x = g.cells_x, cells_y = g.cells_y, eq_w = g.p[0].w, eq_h = g.p[0].h;
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
     const int cy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -80,59 +93,66 @@ __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mas
         hit = true;
     }
     mask[cy * cells_x + cx] = hit ? 1 : 0;
-    if (hit) {   // stamp the tile of every plane that holds this cell
-        int base = 0;
+    if (hit) {   // stamp the tile of every plane that holds this cell, and its coarse tiles
+        int base = 0, cbase = 0;
         for (int p = 0; p < g.planes; ++p) {
             const PlaneGeom &pg = g.p[p];
             const int sh = (pg.sub == 2) ? 3 : 2;   // cells per tile side: 4 (or 8 at half size)
-            tile_gen[base + (cy >> sh) * pg.tiles_x + (cx >> sh)] = gen;
+            const int tx = cx >> sh, ty = cy >> sh;
+            tile_gen[base + ty * pg.tiles_x + tx] = gen;
+            if (pg.ctiles_x > 0) {
+                int cx0, cx1, cy0, cy1;
+                const int q = kTile / 4;   // LL_2 samples per tile side
+                coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, cx0, cx1);
+                coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, cy0, cy1);
+                for (int y = cy0; y <= cy1; ++y)
+                    for (int x = cx0; x <= cx1; ++x) ctile_gen[cbase + y * pg.ctiles_x + x] = gen;
+            }
             base += pg.tiles_x * pg.tiles_y;
+            cbase += pg.ctiles_x * pg.ctiles_y;
         }
     }
 }
 
-// One thread per candidate tile of every plane: a tile is selected when the
-// footprint stamped it with this viewport's generation.  A selected tile also
-// needs the coarse tiles (kCoarseTile samples of LL_2 per axis) that hold its
-// LL_2 window [q t - 3, q t + q + 2] (q = kTile / 4; 9/7 halo, the 5/3 window
-// is narrower), including the window's symmetric extension at the plane
-// edges; the first tile to claim a coarse tile (atomic exchange of its
-// generation stamp) appends it to the coarse list.
-__device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, int &c_hi) {
-    int a = max(lo, 0), b = min(hi, n2 - 1);
-    if (lo < 0) b = max(b, min(-lo, n2 - 1));
-    if (hi > n2 - 1) a = min(a, max(2 * (n2 - 1) - hi, 0));
-    c_lo = a / kCoarseTile;
-    c_hi = b / kCoarseTile;
+// Tile selection: one thread per tile and one per coarse tile of every
+// plane; a (coarse) tile is listed when the footprint stamped it with this
+// viewport's generation.  One atomic per warp reserves list positions.
+__device__ __forceinline__ void append(bool sel, uint32_t entry, uint32_t *list, int *count) {
+    const unsigned ballot = __ballot_sync(0xffffffffu, sel);
+    if (!sel) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(ballot));
+    base = __shfl_sync(ballot, base, leader);
+    list[base + __popc(ballot & ((1u << lane) - 1u))] = entry;
 }
 
 __global__ void k_select_tiles(Geom g, const uint32_t *__restrict__ tile_gen,
-                               uint32_t *__restrict__ ctile_gen, uint32_t gen,
+                               const uint32_t *__restrict__ ctile_gen, uint32_t gen,
                                uint32_t *__restrict__ tiles, uint32_t *__restrict__ ctiles,
                                int *counters) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= g.total_tiles || tile_gen[tid] != gen) return;
-    int plane = 0, t = tid, cbase = 0;
-    while (plane < g.planes - 1 && t >= g.p[plane].tiles_x * g.p[plane].tiles_y) {
-        t -= g.p[plane].tiles_x * g.p[plane].tiles_y;
-        cbase += g.p[plane].ctiles_x * g.p[plane].ctiles_y;
-        ++plane;
+    const bool coarse = tid >= g.total_tiles;
+    const int t0 = coarse ? tid - g.total_tiles : tid;
+    const bool valid = coarse ? t0 < g.total_ctiles : true;
+    bool sel = valid && (coarse ? ctile_gen[t0] : tile_gen[t0]) == gen;
+    uint32_t entry = 0;
+    if (sel) {
+        int plane = 0, t = t0;
+        for (;;) {
+            const PlaneGeom &pg = g.p[plane];
+            const int n = coarse ? pg.ctiles_x * pg.ctiles_y : pg.tiles_x * pg.tiles_y;
+            if (t < n || plane == g.planes - 1) break;
+            t -= n;
+            ++plane;
+        }
+        const int nx = coarse ? g.p[plane].ctiles_x : g.p[plane].tiles_x;
+        entry = ((uint32_t)plane << 28) | ((uint32_t)(t / nx) << 14) | (uint32_t)(t % nx);
     }
-    const PlaneGeom &pg = g.p[plane];
-    const int tx = t % pg.tiles_x, ty = t / pg.tiles_x;
-    const int pos = atomicAdd(&counters[0], 1);
-    tiles[pos] = ((uint32_t)plane << 28) | ((uint32_t)ty << 14) | (uint32_t)tx;
-    if (pg.ctiles_x == 0) return;
-    int cx0, cx1, cy0, cy1;
-    const int q = kTile / 4;   // LL_2 samples per tile side
-    coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, cx0, cx1);
-    coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, cy0, cy1);
-    for (int cy = cy0; cy <= cy1; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx)
-            if (atomicExch(&ctile_gen[cbase + cy * pg.ctiles_x + cx], gen) != gen) {
-                const int cpos = atomicAdd(&counters[1], 1);
-                ctiles[cpos] = ((uint32_t)plane << 28) | ((uint32_t)cy << 14) | (uint32_t)cx;
-            }
+    // warps straddling the two ranges: both calls are made by all lanes
+    append(sel && !coarse, entry, tiles, &counters[0]);
+    append(sel && coarse, entry, ctiles, &counters[1]);
 }
 
 __global__ void k_all_tiles(int plane, int tiles_x, int tiles_y, uint32_t *tiles,
@@ -156,18 +176,18 @@ __global__ void k_project(View v, float *uv) {
 }  // namespace
 
 void launch_footprint(const Geom &g, const View &v, uint8_t *mask, uint32_t *tile_gen,
-                      uint32_t gen, int *counters, cudaStream_t cs) {
+                      uint32_t *ctile_gen, uint32_t gen, int *counters, cudaStream_t cs) {
     const Frustum f = make_frustum(v);
     dim3 block(32, 8);
     dim3 grid((g.cells_x + 31) / 32, (g.cells_y + 7) / 8);
-    k_footprint<<<grid, block, 0, cs>>>(v, f, g, mask, tile_gen, gen, counters);
+    k_footprint<<<grid, block, 0, cs>>>(v, f, g, mask, tile_gen, ctile_gen, gen, counters);
 }
 
-void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, uint32_t *ctile_gen,
+void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, const uint32_t *ctile_gen,
                          uint32_t gen, uint32_t *tiles, uint32_t *ctiles, int *counters,
                          cudaStream_t cs) {
     const int threads = 256;
-    const int blocks = (g.total_tiles + threads - 1) / threads;
+    const int blocks = (g.total_tiles + g.total_ctiles + threads - 1) / threads;
     k_select_tiles<<<blocks > 0 ? blocks : 1, threads, 0, cs>>>(g, tile_gen, ctile_gen, gen, tiles,
                                                                 ctiles, counters);
 }

@@ -512,6 +512,87 @@ __device__ __forceinline__ void column_segment(const float *A, int sa, int col, 
     }
 }
 
+// Same as column_segment for two adjacent columns (col even: one 8-byte
+// shared load per row for both); emit(i, v0, v1).
+template <int WAV, class Emit>
+__device__ __forceinline__ void column_pair(const float *A, int sa, int col, int rows, int r_a,
+                                            int r_b, Emit emit) {
+    constexpr int VV = Traits<WAV>::V;
+    int i = max(0, (r_a - VV) & ~1);
+    const float2 *p = reinterpret_cast<const float2 *>(A + col);
+    const int s2 = sa / 2;
+    if constexpr (WAV == 1) {
+        float2 po = p[(i + 1) * s2];
+        float2 y1p = {0.f, 0.f}, y2pp = {0.f, 0.f}, y3pp = {0.f, 0.f}, y4m = {0.f, 0.f};
+        auto step = [&](int r) {
+            const float2 e = p[r * s2];
+            const float2 o = p[(r + 1) * s2];
+            float2 y1k, y2m, y3m;
+            y1k.x = fmaf(-kDelta, po.x + o.x, e.x);
+            y1k.y = fmaf(-kDelta, po.y + o.y, e.y);
+            y2m.x = fmaf(-kGamma, y1p.x + y1k.x, po.x);
+            y2m.y = fmaf(-kGamma, y1p.y + y1k.y, po.y);
+            y3m.x = fmaf(-kBeta, y2pp.x + y2m.x, y1p.x);
+            y3m.y = fmaf(-kBeta, y2pp.y + y2m.y, y1p.y);
+            y4m.x = fmaf(-kAlpha, y3pp.x + y3m.x, y2pp.x);
+            y4m.y = fmaf(-kAlpha, y3pp.y + y3m.y, y2pp.y);
+            const float2 out_even = y3pp;
+            y3pp = y3m;
+            y2pp = y2m;
+            y1p = y1k;
+            po = o;
+            return out_even;
+        };
+        for (; i < r_a + 3; i += 2) step(i);
+        if (i == r_a + 3) {
+            step(i);
+            emit(i - 3, y4m.x, y4m.y);
+            i += 2;
+        }
+        for (; i <= r_b + 2; i += 2) {
+            const float2 ev = step(i);
+            emit(i - 4, ev.x, ev.y);
+            emit(i - 3, y4m.x, y4m.y);
+        }
+        if (i - 4 <= r_b - 1 && i + 1 < rows) {
+            const float2 ev = step(i);
+            emit(i - 4, ev.x, ev.y);
+        }
+    } else {
+        const int2 *pi = reinterpret_cast<const int2 *>(p);
+        int2 po = pi[(i + 1) * s2];
+        int2 y1p = {0, 0}, y2m = {0, 0};
+        auto step = [&](int r) {
+            const int2 e = pi[r * s2];
+            const int2 o = pi[(r + 1) * s2];
+            int2 y1k;
+            y1k.x = e.x - ((po.x + o.x + 2) >> 2);
+            y1k.y = e.y - ((po.y + o.y + 2) >> 2);
+            y2m.x = po.x + ((y1p.x + y1k.x) >> 1);
+            y2m.y = po.y + ((y1p.y + y1k.y) >> 1);
+            const int2 out_even = y1p;
+            y1p = y1k;
+            po = o;
+            return out_even;
+        };
+        for (; i < r_a + 1; i += 2) step(i);
+        if (i == r_a + 1) {
+            step(i);
+            emit(i - 1, __int_as_float(y2m.x), __int_as_float(y2m.y));
+            i += 2;
+        }
+        for (; i <= r_b; i += 2) {
+            const int2 ev = step(i);
+            emit(i - 2, __int_as_float(ev.x), __int_as_float(ev.y));
+            emit(i - 1, __int_as_float(y2m.x), __int_as_float(y2m.y));
+        }
+        if (i - 2 <= r_b - 1 && i + 1 < rows) {
+            const int2 ev = step(i);
+            emit(i - 2, __int_as_float(ev.x), __int_as_float(ev.y));
+        }
+    }
+}
+
 template <int WAV, int NB>
 __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
     constexpr int H = Traits<WAV>::H;
@@ -551,6 +632,57 @@ __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
             const int nv = G.ox.hi - G.ox.lo + 1;
             const int r0 = G.oy.lo - 2 * G.ky.lo, r1 = G.oy.hi - 2 * G.ky.lo + 1;
             const int jc0 = G.ox.lo - 2 * G.kx0 - G.ja4;   // A column of output ox.lo (unswizzled)
+            if ((jc0 & 1) == 0 && (nv & 1) == 0) {
+                // column pairs: both columns of a pair sit in one 8-byte slot of
+                // the swizzled row (swz keeps j and j + 1 together for even j)
+                const int np = nv / 2;
+                const int nseg = max(1, min((int)blockDim.x / np, (r1 - r0) / 16));
+                const int items = np * nseg;
+                for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                    const int jp = it % np, sg = it / np;
+                    const int ra = r0 + (r1 - r0) * sg / nseg, rb = r0 + (r1 - r0) * (sg + 1) / nseg;
+                    const int x = G.ox.lo + 2 * jp;
+                    const int col = swz(jc0 + 2 * jp);
+                    if (l > a.l_bot) {
+                        float *dst = P + (x - pn.col0);
+                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                            float *d = dst + (2 * G.ky.lo + i - G.oy.lo) * pn.stride;
+                            d[0] = v0;
+                            d[1] = v1;
+                        });
+                    } else if (a.l_bot > 1) {
+                        float *dst = a.ll_out[plane] + x;
+                        const int pitch = a.ll_out_pitch[plane];
+                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                            float *d = dst + (size_t)(2 * G.ky.lo + i) * pitch;
+                            d[0] = v0;
+                            d[1] = v1;
+                        });
+                    } else if (a.out_f32 && plane == a.f32_plane) {
+                        float *o = a.out_f32 + x;
+                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                            float *d = o + (size_t)(2 * G.ky.lo + i) * pg.w;
+                            d[0] = ((WAV == 1) ? v0 : (float)__float_as_int(v0)) + 128.0f;
+                            d[1] = ((WAV == 1) ? v1 : (float)__float_as_int(v1)) + 128.0f;
+                        });
+                    } else {
+                        uint8_t *o = a.out_u8[plane] + x;
+                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                            int p0, p1;
+                            if constexpr (WAV == 1) {
+                                p0 = __float2int_rd(v0 + 128.5f);
+                                p1 = __float2int_rd(v1 + 128.5f);
+                            } else {
+                                p0 = __float_as_int(v0) + 128;
+                                p1 = __float_as_int(v1) + 128;
+                            }
+                            const unsigned short w = (unsigned short)(min(max(p0, 0), 255) |
+                                                                      (min(max(p1, 0), 255) << 8));
+                            *reinterpret_cast<unsigned short *>(o + (size_t)(2 * G.ky.lo + i) * pg.w) = w;
+                        });
+                    }
+                }
+            } else {
             const int nseg = max(1, min((int)blockDim.x / nv, (r1 - r0) / 16));
             const int items = nv * nseg;
             for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -583,6 +715,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
                         o[(size_t)(2 * G.ky.lo + i) * pg.w] = (uint8_t)min(max(p, 0), 255);
                     });
                 }
+            }
             }
             __syncthreads();
         }

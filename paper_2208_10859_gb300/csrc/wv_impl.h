@@ -97,8 +97,8 @@ Frustum make_frustum(const View &v);
 
 // kernel launchers
 void launch_footprint(const Geom &g, const View &v, uint8_t *mask, uint32_t *tile_gen,
-                      uint32_t gen, int *counters, cudaStream_t cs);
-void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, uint32_t *ctile_gen,
+                      uint32_t *ctile_gen, uint32_t gen, int *counters, cudaStream_t cs);
+void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, const uint32_t *ctile_gen,
                          uint32_t gen, uint32_t *tiles, uint32_t *ctiles, int *counters,
                          cudaStream_t cs);
 void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
