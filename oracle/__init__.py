@@ -27,6 +27,9 @@ What is computed, with the passage each part follows:
 * ``footprint`` -- the low-resolution binary reconstruction mask (Sec. 3.1:
   256x256 cells for an 8k frame, i.e. 32-pixel cells).
 * ``cone`` -- coefficients the masked iFWT needs (Sec. 3.1/3.4).
+* ``fovea_distance`` / ``fovea_keep`` / ``fovea_coef_mask`` -- foveated
+  decoding (Sec. 3.7): finer levels' details only near the gaze, rectilinear
+  regions, dropped coefficients taken as zero.
 * ``resample`` / ``ycbcr_to_rgba`` / ``viewport`` -- reprojection of the
   decoded region into the viewport (Sec. 3.6) with bilinear filtering and a
   BT.709 colour conversion (the paper itself does none, Sec. 5).
@@ -428,25 +431,30 @@ def frame_slots(p: Params, frame: int) -> list[tuple[int, int]]:
     return [(s * n + slot, bit) for (slot, j, bit) in haar_needed_slots(p.tlevels, fl)]
 
 
-def decode_coefs(st: Stream, frame: int, plane: int):
-    """Dequantised, temporally rebuilt Mallat plane of one frame (Sec. 3.5)."""
+def decode_coefs(st: Stream, frame: int, plane: int, keep=None):
+    """Dequantised, temporally rebuilt Mallat plane of one frame (Sec. 3.5).
+    keep: optional foveation cell masks (see ``fovea_keep``); coefficients
+    they drop are taken as zero (Sec. 3.7)."""
     p = st.p
     integer = p.wavelet == WAVELET_53
     n = 1 << p.tlevels
     bands = [dequantize(st.coef_plane(t, plane), p.step, integer)
              for (t, bit) in frame_slots(p, frame)]
+    if keep is not None:
+        m = fovea_coef_mask(p, plane, keep)
+        bands = [b * m for b in bands]
     if p.tlevels == 0:
         return bands[0]
     return haar_inverse(bands, p.tlevels, frame % n, integer)
 
 
-def decode_plane(st: Stream, frame: int, plane: int):
+def decode_plane(st: Stream, frame: int, plane: int, keep=None):
     """Full-frame reconstruction of one plane.  Returns (x, u8): x are the
     samples in 8-bit units before rounding (float64 for 9/7, int64 for 5/3,
     DC unshifted) and u8 the 8-bit result: clip(floor(x + 1/2)) for 9/7,
-    clip(x) for 5/3."""
+    clip(x) for 5/3.  keep: optional foveation cell masks."""
     p = st.p
-    c = decode_coefs(st, frame, plane)
+    c = decode_coefs(st, frame, plane, keep)
     x = inv2d(c, p.levels, p.wavelet) + 128
     if p.wavelet == WAVELET_97:
         u8 = np.clip(np.floor(x + 0.5), 0, 255).astype(np.uint8)
@@ -622,10 +630,11 @@ def cell_mask_to_pixels(mask: np.ndarray, w: int, h: int) -> np.ndarray:
     return np.repeat(np.repeat(mask.astype(bool), ry, axis=0), rx, axis=1)
 
 
-def cone_bytes(st: Stream, frame: int, mask: np.ndarray) -> int:
+def cone_bytes(st: Stream, frame: int, mask: np.ndarray, keep=None) -> int:
     """Coefficient bytes the viewport needs: the cone of the mask in every
     plane, restricted to stored (non-zero) blocks, 2 bytes per coefficient,
-    summed over the coefficient frames the inter-frame rebuild reads."""
+    summed over the coefficient frames the inter-frame rebuild reads.  With
+    foveation cell masks `keep`, coefficients they drop are not read."""
     p = st.p
     total = 0
     for pl in range(p.planes):
@@ -634,9 +643,78 @@ def cone_bytes(st: Stream, frame: int, mask: np.ndarray) -> int:
         full = np.zeros((h, w), bool)
         for (name, lev, x0, y0, sw, sh) in subbands(w, h, p.levels):
             full[y0:y0 + sh, x0:x0 + sw] = need[(name, lev)]
+        if keep is not None:
+            full &= fovea_coef_mask(p, pl, keep)
         for (t, _bit) in frame_slots(p, frame):
             total += 2 * int(np.count_nonzero(full & st.present_mask(t, pl)))
     return total
+
+
+# --------------------------------------------------------------------------
+# foveated decoding (Sec. 3.7)
+# --------------------------------------------------------------------------
+#
+# The full viewport is reconstructed from the coarse levels; each finer level
+# adds its details only over a smaller, rectilinear region around the gaze,
+# and the inverse transform treats the dropped details as zero.  The regions
+# are unions of mask cells: a cell keeps the details of level l when its
+# centre lies within r_l of the gaze, the distance being the larger of the
+# horizontal and vertical angle differences seen from the viewer (squares in
+# angle, i.e. rectilinear regions).  Level 1 (finest) uses r1, level 2 uses
+# r2; coarser levels are always complete.  A detail coefficient belongs to the
+# cell of its nominal position: coefficient (kx, ky) of a level-l subband of a
+# plane subsampled by s sits at luma pixel (s kx 2^l, s ky 2^l).
+
+
+def fovea_distance(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: float,
+                   cell: int = CELL) -> np.ndarray:
+    """Per mask cell (rows x cols), the angular distance (radians) of the
+    cell centre from the gaze direction: max(|theta_x - gaze_x|,
+    |theta_y - gaze_y|), theta_x = atan2(x, z) and theta_y = atan2(y, z) in
+    viewer coordinates (x right, y up, z forward; gaze angles relative to the
+    view centre).  Cells behind the viewer (z <= 0) are infinitely far."""
+    W, H = p.width, p.height
+    rows, cols = H // cell, W // cell
+    lon = 2 * math.pi * ((np.arange(cols) + 0.5) * cell / W - 0.5)
+    lat = math.pi * (0.5 - (np.arange(rows) + 0.5) * cell / H)
+    LON, LAT = np.meshgrid(lon, lat)
+    d = np.stack([np.cos(LAT) * np.sin(LON), np.sin(LAT), np.cos(LAT) * np.cos(LON)], axis=-1)
+    cam = d @ rotation(yaw, pitch)          # rows of R^T d: world -> viewer
+    tx = np.arctan2(cam[..., 0], cam[..., 2])
+    ty = np.arctan2(cam[..., 1], cam[..., 2])
+    dist = np.maximum(np.abs(tx - gaze_x), np.abs(ty - gaze_y))
+    return np.where(cam[..., 2] > 0, dist, np.inf)
+
+
+def fovea_keep(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: float,
+               r1: float, r2: float) -> dict:
+    """Cell masks of the detail levels foveation keeps: {1: dist <= r1,
+    2: dist <= r2}; other levels are complete."""
+    d = fovea_distance(p, yaw, pitch, gaze_x, gaze_y)
+    return {1: d <= r1, 2: d <= r2}
+
+
+def fovea_coef_mask(p: Params, plane: int, keep: dict) -> np.ndarray:
+    """Boolean Mallat-plane mask of the coefficients foveation keeps."""
+    w, h = plane_dims(p, plane)
+    s = 2 if (plane > 0 and p.chroma_420) else 1
+    out = np.ones((h, w), bool)
+    for (name, lev, x0, y0, sw, sh) in subbands(w, h, p.levels):
+        if name == "LL" or lev not in keep:
+            continue
+        cx = (np.arange(sw) * s << lev) // CELL
+        cy = (np.arange(sh) * s << lev) // CELL
+        out[y0:y0 + sh, x0:x0 + sw] = keep[lev][np.ix_(cy, cx)]
+    return out
+
+
+def fovea_margin(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: float,
+                 r1: float, r2: float) -> float:
+    """Smallest |distance - radius| over all cells (radians): how far the
+    keep decisions are from a tie."""
+    d = fovea_distance(p, yaw, pitch, gaze_x, gaze_y)
+    d = d[np.isfinite(d)]
+    return float(min(np.abs(d - r1).min(), np.abs(d - r2).min())) if d.size else math.inf
 
 
 # --------------------------------------------------------------------------
@@ -680,13 +758,15 @@ def resample(planes, p: Params, u, v) -> np.ndarray:
 
 
 def viewport(st: Stream, frame: int, yaw: float, pitch: float, fov: float,
-             out_w: int, out_h: int, planes=None) -> np.ndarray:
+             out_w: int, out_h: int, planes=None, fovea=None) -> np.ndarray:
     """Reference viewport decode by the plain definition: reconstruct the
-    whole frame, then reproject it into the viewport.  Returns RGBA uint8
+    whole frame, then reproject it into the viewport.  fovea = (gaze_x,
+    gaze_y, r1, r2) decodes with foveation (Sec. 3.7).  Returns RGBA uint8
     (out_h, out_w, 4)."""
     p = st.p
     if planes is None:
-        planes = [decode_plane(st, frame, pl)[1] for pl in range(p.planes)]
+        keep = None if fovea is None else fovea_keep(p, yaw, pitch, *fovea)
+        planes = [decode_plane(st, frame, pl, keep)[1] for pl in range(p.planes)]
     u, v = project(out_w, out_h, yaw, pitch, fov, p.width, p.height)
     return resample(planes, p, u, v)
 
