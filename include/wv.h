@@ -141,19 +141,117 @@ const char *wv_strerror(int code);
 int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch,
                        float fov, const wv_image *out);
 
-/* One viewport request of a batch. */
+/* One viewport request of a batch.  The fields after `out` select foveated
+ * decoding (Sec. 3.7): with fovea = 1 the details of wavelet level 1 (the
+ * finest) are decoded only in mask cells whose centre lies within r1 of the
+ * gaze and those of level 2 only within r2; elsewhere they are taken as zero
+ * and the inverse transform still runs over the whole viewport.  The
+ * distance of a cell is the larger of its horizontal and vertical angle from
+ * the gaze as the viewer sees it (x right, y up, z forward:
+ * max(|atan2(x, z) - gaze_x|, |atan2(y, z) - gaze_y|)), so the regions are
+ * rectilinear; cells behind the viewer count as infinitely far.  gaze_x and
+ * gaze_y are radians relative to the view centre; r1 and r2 are radians (a
+ * negative radius keeps nothing of its level, an infinite one everything).
+ * With fovea = 0 the gaze fields are ignored. */
 typedef struct {
     wv_stream *s;
     int frame;
     float yaw, pitch, fov;
     wv_image out;
+    int fovea;
+    float gaze_x, gaze_y;
+    float r1, r2;
 } wv_request;
 
-/* Decode n viewport requests, possibly of different streams, enqueued on
- * cuda_stream (NULL = legacy default stream).  Each result equals the
- * result of wv_decode_viewport for the same request.  Requests sharing a
- * wv_stream are decoded one after the other. */
+/* Decode n viewport requests, possibly of different streams, sizes, fields
+ * of view and foveation settings, as one batch enqueued on cuda_stream
+ * (NULL = legacy default stream): one CUDA graph whose tile decode is one
+ * persistent launch per decode class (see wv_batch_decode).  Each result
+ * equals the result of wv_decode_viewport for the same request (foveated
+ * requests: of the foveated decode).  Uses a batch context per device that
+ * the library creates on first use and keeps until
+ * wv_release_default_batch(); calls from several host threads are
+ * serialised.  Returns WV_ERR_ARG for an invalid request (the fields checked
+ * by wv_decode_viewport, fovea not 0/1, a non-finite gaze or NaN radius) and
+ * WV_ERR_OOM when the batch's device memory cannot be allocated. */
 int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream);
+
+/* Release the per-device contexts of wv_decode_batch (waits for their work). */
+void wv_release_default_batch(void);
+
+/* ---------------------------------------------------------------------------
+ * Batch contexts (batched decoding with explicit control)
+ * ------------------------------------------------------------------------- */
+
+typedef struct wv_batch wv_batch;
+
+/* Statistics of the last wv_batch_decode. */
+typedef struct {
+    int requests;        /* requests of the batch */
+    int surfaces;        /* decode targets: distinct (stream, frame) of the
+                            unfoveated requests + one per foveated request */
+    int coarse_tiles;    /* coarse tiles decoded (levels L..3) */
+    int fine_tiles;      /* output tiles decoded (levels 2..1) */
+    size_t bytes;        /* device memory held by the context */
+    double ms[4];        /* with wv_batch_set_timing(b, 1): footprint, tile
+                            lists, tile decode, reprojection (milliseconds) */
+} wv_batch_info;
+
+/* Create a batch context on the current device whose launches go to
+ * cuda_stream (NULL = legacy default stream).  The context allocates its
+ * device memory (per decode target: reconstruction and LL_2 planes, tile
+ * stamps and lists) and a pinned host staging buffer on demand, growing them
+ * when a batch needs more; it never shrinks them before wv_batch_close. */
+int wv_batch_create(void *cuda_stream, wv_batch **out);
+
+/* Wait for the context's work and free it. */
+void wv_batch_close(wv_batch *b);
+
+/* Decode n requests as one batch: one CUDA graph of (1) the upload of the
+ * job tables from pinned host memory, (2) clearing of stamps and counters,
+ * (3) the footprint of every request, (4) the tile lists of every decode
+ * target, (5) per decode class (wavelet and 1 + tlevels coefficient
+ * frames) one
+ * persistent tile-decode launch over every coarse tile (levels L..3), then
+ * every output tile (levels 2..1) of its targets, and (6) the reprojection
+ * of every request.  Unfoveated requests of the same stream and frame share
+ * one decode target, so a tile several of them need is decoded once.  The
+ * graph is reused while the batch keeps its shape; the call returns before
+ * the GPU finishes (outputs valid once the context's CUDA stream is
+ * synchronised).  The streams and output images must stay alive until then;
+ * the request array may be reused as soon as the call returns. */
+int wv_batch_decode(wv_batch *b, const wv_request *reqs, int n);
+
+/* Use another CUDA stream for later launches (ordered after the earlier ones). */
+int wv_batch_set_cuda_stream(wv_batch *b, void *cuda_stream);
+
+/* Device bytes a batch of these requests needs in the context (admission
+ * control: a server can compare it with the free device memory). */
+int wv_batch_device_bytes(wv_batch *b, const wv_request *reqs, int n, size_t *bytes);
+
+/* Wait for the context's last batch and read its device error word: WV_OK,
+ * or the first error a kernel recorded (WV_ERR_TIMEOUT: a bounded wait of
+ * the tile decode gave up; WV_ERR_DEVICE: an internal size check failed);
+ * the word is then cleared. */
+int wv_batch_sync_status(wv_batch *b);
+
+/* Wait for the last batch and report its statistics. */
+int wv_batch_stats(wv_batch *b, wv_batch_info *info);
+
+/* on = 1: run batches as direct launches with CUDA events between the steps
+ * (wv_batch_stats reports per-step times); on = 0: CUDA graph (default). */
+int wv_batch_set_timing(wv_batch *b, int on);
+
+/* Tile shapes: output tile side (64 or 128 samples) and coarse tile side (32
+ * or 64 samples of LL_2) for streams with this wavelet, level count and luma
+ * size.  Default 128 / 64.  wv_batch_autotune times each of the four shapes
+ * on the given requests (reps timed launches after one warm-up per shape, one
+ * (wavelet, levels, size) class at a time) and keeps the fastest. */
+int wv_batch_set_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height,
+                            int tile, int ctile);
+int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile,
+                        int *ctile);
+int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps);
 
 /* Decode a whole plane of one frame (all tiles) -- the full-frame case, used
  * for the lossless workload and for parity checks.  dptr receives width x

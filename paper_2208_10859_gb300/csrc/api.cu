@@ -271,8 +271,9 @@ unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask
 
 namespace wv {
 
-int build_geom(const wv_stream_desc &d, Geom *g) {
+int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     memset(g, 0, sizeof(*g));
+    if ((tile != 64 && tile != 128) || (ctile != 32 && ctile != 64)) return WV_ERR_ARG;
     if (d.planes != 1 && d.planes != 3) return WV_ERR_ARG;
     if (d.chroma_420 != 0 && d.chroma_420 != 1) return WV_ERR_ARG;
     if (d.levels < 1 || d.levels > kMaxLevels) return WV_ERR_ARG;
@@ -297,6 +298,8 @@ int build_geom(const wv_stream_desc &d, Geom *g) {
     g->step = d.step;
     g->cells_x = d.width / kCell;
     g->cells_y = d.height / kCell;
+    g->tile = tile;
+    g->ctile = ctile;
     int id = 0;
     g->total_tiles = 0;
     g->total_ctiles = 0;
@@ -320,13 +323,15 @@ int build_geom(const wv_stream_desc &d, Geom *g) {
                 pg.base[l][s] = id;
                 id += pg.nbx[l] * pg.nby[l];
             }
-        pg.tiles_x = (pg.w + kTile - 1) / kTile;
-        pg.tiles_y = (pg.h + kTile - 1) / kTile;
+        pg.tiles_x = (pg.w + tile - 1) / tile;
+        pg.tiles_y = (pg.h + tile - 1) / tile;
         g->total_tiles += pg.tiles_x * pg.tiles_y;
+        pg.tile_shift = 0;   // a tile spans tile * sub / 32 mask cells per side
+        while ((kCell << pg.tile_shift) < tile * pg.sub) ++pg.tile_shift;
         pg.ll2_pitch = (((pg.w >> 2) + 7) / 8) * 8;
         if (d.levels >= 3) {
-            pg.ctiles_x = ((pg.w >> 2) + kCoarseTile - 1) / kCoarseTile;
-            pg.ctiles_y = ((pg.h >> 2) + kCoarseTile - 1) / kCoarseTile;
+            pg.ctiles_x = ((pg.w >> 2) + ctile - 1) / ctile;
+            pg.ctiles_y = ((pg.h >> 2) + ctile - 1) / ctile;
         }
         g->total_ctiles += pg.ctiles_x * pg.ctiles_y;
     }
@@ -437,6 +442,7 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     wv_stream *s = new (std::nothrow) wv_stream();
     if (!s) return WV_ERR_OOM;
     build_geom(d, &s->g);
+    s->desc = d;
     cudaGetDevice(&s->device);
     s->cs = (cudaStream_t)cuda_stream;
     s->n_payload = h.n_payload;
@@ -509,22 +515,6 @@ void wv_close_stream(wv_stream *s) {
 int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
                        const wv_image *out) {
     return decode_viewport(s, frame, yaw, pitch, fov, out);
-}
-
-int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream) {
-    if (n < 0 || (n > 0 && !reqs)) return WV_ERR_ARG;
-    for (int i = 0; i < n; ++i)
-        if (!reqs[i].s) return WV_ERR_ARG;
-    for (int i = 0; i < n; ++i) {
-        wv_stream *s = reqs[i].s;
-        cudaStream_t saved = s->cs;
-        s->cs = (cudaStream_t)cuda_stream;
-        const int rc = decode_viewport(s, reqs[i].frame, reqs[i].yaw, reqs[i].pitch, reqs[i].fov,
-                                       &reqs[i].out);
-        s->cs = saved;
-        if (rc != WV_OK) return rc;
-    }
-    return WV_OK;
 }
 
 int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float) {

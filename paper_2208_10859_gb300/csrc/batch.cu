@@ -1,0 +1,612 @@
+// batch.cu -- batched viewport decoding: many requests over several streams
+// of uneven size, field of view and foveation in one CUDA graph.
+//
+// One batch is one graph of six steps on the batch's CUDA stream:
+//   1. upload of the job tables (one copy from pinned host memory);
+//   2. clearing of the tile stamps and work counters;
+//   3. footprint of every request (k_footprint_batch, one grid slice each);
+//   4. tile lists of every decode target (k_select_batch);
+//   5. per decode class (wavelet, number of coefficient frames the
+//      inter-frame rebuild reads) one persistent tile-decode launch over all
+//      coarse, then all fine tiles of its targets (k_tiles_batch);
+//   6. reprojection of every request (k_resample_batch).
+// Requests of the same stream and frame without foveation share one decode
+// target ("surface"), so a tile that several viewports need is decoded once.
+// A foveated request (Sec. 3.7) has a surface of its own, since the details
+// it drops depend on its gaze.  The instantiated graph is kept and relaunched
+// while the batch keeps its shape (counts, sizes, arena); between launches
+// only the job tables change.
+//
+// Tile shapes (output tile 64 or 128 samples, coarse tile 32 or 64 samples
+// of LL_2) are chosen per (wavelet, levels, frame size) by an autotuner that
+// times the batch with each shape (wv_batch_autotune).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wv_impl.h"
+
+using namespace wv;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+using TuneKey = std::array<int, 4>;   // wavelet, levels, width, height
+
+struct Surface {
+    wv_stream *s;
+    int frame;
+    bool foveated;
+    Geom g;
+    int cls;
+    size_t recon[3], ll2[3], fmask, stamp;
+};
+
+struct Plan {
+    std::vector<Surface> surf;
+    std::vector<int> req_surface;
+    size_t jobs, reqs, ctr, stamps, lists_c[kClasses], lists_f[kClasses], err, total;
+    size_t clear_bytes;   // counters + stamps, cleared every launch
+    int n_ctr;
+    int max_cx, max_cy, max_stamps, max_w, max_h;
+    int smem[kClasses];   // dynamic shared memory of each class's decode (0: class absent)
+    size_t job_bytes;
+};
+
+}  // namespace
+
+struct wv_batch {
+    int device = 0;
+    cudaStream_t cs = nullptr;         // stream of the last launch
+    cudaStream_t cap = nullptr;        // private stream for graph capture
+    char *dmem = nullptr;
+    size_t dbytes = 0;
+    char *host = nullptr;              // pinned job-table staging
+    size_t hbytes = 0;
+    cudaEvent_t staged = nullptr;      // the last launch's upload has finished
+    cudaEvent_t done = nullptr;        // the last launch has finished
+    bool launched = false;
+    bool use_graph = true;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> shape;      // key of the instantiated graph
+    std::map<TuneKey, std::pair<int, int>> tuned;
+    int *err = nullptr;
+    // statistics of the last launch (read back on request)
+    int last_requests = 0, last_surfaces = 0;
+    int *ctr_dev = nullptr;
+    int n_ctr = 0;
+    // per-step timing of the last launch (direct mode only)
+    bool timing = false;
+    cudaEvent_t ev[5] = {};
+};
+
+namespace {
+
+int check_request(const wv_request &r) {
+    if (!r.s) return WV_ERR_ARG;
+    if (r.frame < 0 || r.frame >= r.s->g.num_frames) return WV_ERR_ARG;
+    if (!(r.fov > 0.f && r.fov < 3.14159f) || !isfinite(r.yaw) || !isfinite(r.pitch)) return WV_ERR_ARG;
+    const wv_image *o = &r.out;
+    if (!o->dptr || o->width <= 0 || o->height <= 0 || o->pitch_bytes < (size_t)o->width * 4 ||
+        (o->pitch_bytes % 4) != 0 || ((uintptr_t)o->dptr % 4) != 0)
+        return WV_ERR_ARG;
+    if (r.fovea != 0 && r.fovea != 1) return WV_ERR_ARG;
+    if (r.fovea && (!isfinite(r.gaze_x) || !isfinite(r.gaze_y) || isnan(r.r1) || isnan(r.r2)))
+        return WV_ERR_ARG;
+    return WV_OK;
+}
+
+std::pair<int, int> tile_shape(const wv_batch *b, const Geom &g) {
+    auto it = b->tuned.find(TuneKey{g.wavelet, g.levels, g.p[0].w, g.p[0].h});
+    return it == b->tuned.end() ? std::make_pair(kTile, kCoarseTile) : it->second;
+}
+
+int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
+    std::map<std::pair<const wv_stream *, int>, int> shared;
+    P.surf.clear();
+    P.req_surface.assign(n, -1);
+    for (int i = 0; i < n; ++i) {
+        const wv_request &r = reqs[i];
+        if (!r.fovea) {
+            auto it = shared.find({r.s, r.frame});
+            if (it != shared.end()) {
+                P.req_surface[i] = it->second;
+                continue;
+            }
+        }
+        Surface S{};
+        S.s = r.s;
+        S.frame = r.frame;
+        S.foveated = r.fovea != 0;
+        const Geom &sg = r.s->g;
+        const std::pair<int, int> ts = tile_shape(b, sg);
+        if (build_geom(r.s->desc, &S.g, ts.first, ts.second) != WV_OK) return WV_ERR_ARG;
+        // 1 + tlevels coefficient frames
+        S.cls = 2 * kMaxBands * S.g.wavelet + kMaxBands * (S.foveated ? 1 : 0) + S.g.tlevels;
+        P.req_surface[i] = (int)P.surf.size();
+        if (!r.fovea) shared[{r.s, r.frame}] = (int)P.surf.size();
+        P.surf.push_back(S);
+    }
+    const int m = (int)P.surf.size();
+    // arena: error word | job tables | counters | stamps | lists | per-surface
+    // planes.  The error word stays at offset 0 for every plan.
+    P.err = 0;
+    size_t o = 256;
+    P.jobs = o;
+    o = align256(o + sizeof(SurfaceJob) * m);
+    P.reqs = o;
+    o = align256(o + sizeof(RequestJob) * n);
+    P.job_bytes = o;
+    P.ctr = o;
+    P.n_ctr = kBatchCtr + 2 * m;
+    o += sizeof(int) * P.n_ctr;
+    P.stamps = o;
+    size_t tiles[kClasses] = {}, ctiles[kClasses] = {};
+    P.max_cx = P.max_cy = P.max_stamps = 0;
+    for (Surface &S : P.surf) {
+        S.stamp = o;
+        o += sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
+        tiles[S.cls] += S.g.total_tiles;
+        ctiles[S.cls] += S.g.total_ctiles;
+        P.max_cx = std::max(P.max_cx, S.g.cells_x);
+        P.max_cy = std::max(P.max_cy, S.g.cells_y);
+        P.max_stamps = std::max(P.max_stamps, S.g.total_tiles + S.g.total_ctiles);
+    }
+    P.clear_bytes = o - P.ctr;
+    o = align256(o);
+    for (int c = 0; c < kClasses; ++c) {
+        P.lists_c[c] = o;
+        o = align256(o + sizeof(uint2) * std::max<size_t>(ctiles[c], 1));
+        P.lists_f[c] = o;
+        o = align256(o + sizeof(uint2) * std::max<size_t>(tiles[c], 1));
+    }
+    for (Surface &S : P.surf) {
+        for (int p = 0; p < 3; ++p) {
+            S.recon[p] = o;
+            if (p < S.g.planes) o = align256(o + (size_t)S.g.p[p].w * S.g.p[p].h);
+        }
+        for (int p = 0; p < 3; ++p) {
+            S.ll2[p] = o;
+            if (p < S.g.planes && S.g.levels >= 3)
+                o = align256(o + (size_t)S.g.p[p].ll2_pitch * (S.g.p[p].h >> 2) * 4);
+        }
+        S.fmask = o;
+        if (S.foveated) o = align256(o + (size_t)S.g.cells_x * S.g.cells_y);
+    }
+    P.total = o;
+    P.max_w = P.max_h = 0;
+    for (int i = 0; i < n; ++i) {
+        P.max_w = std::max(P.max_w, reqs[i].out.width);
+        P.max_h = std::max(P.max_h, reqs[i].out.height);
+    }
+    for (int c = 0; c < kClasses; ++c) P.smem[c] = 0;
+    return WV_OK;
+}
+
+TileArgs pass_args(const Surface &S, char *base, int *err, bool coarse) {
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = S.g;
+    a.payload = S.s->payload;
+    a.table = S.s->table;
+    a.bands = frame_bands(S.g, S.frame);
+    a.err = err;
+    a.f32_plane = -1;
+    a.fmask = S.foveated ? (const uint8_t *)(base + S.fmask) : nullptr;
+    const bool split = S.g.levels >= 3;
+    if (coarse) {
+        a.l_top = S.g.levels;
+        a.l_bot = 3;
+        a.tile = S.g.ctile;
+        for (int p = 0; p < S.g.planes; ++p) {
+            a.ll_out[p] = (float *)(base + S.ll2[p]);
+            a.ll_out_pitch[p] = S.g.p[p].ll2_pitch;
+        }
+    } else {
+        a.l_top = split ? 2 : S.g.levels;
+        a.l_bot = 1;
+        a.tile = S.g.tile;
+        for (int p = 0; p < S.g.planes; ++p) {
+            a.out_u8[p] = (uint8_t *)(base + S.recon[p]);
+            if (split) {
+                a.ll_in[p] = (const float *)(base + S.ll2[p]);
+                a.ll_in_pitch[p] = S.g.p[p].ll2_pitch;
+            }
+        }
+    }
+    fill_tile_scales(a);
+    return a;
+}
+
+// Fill the host job tables (pinned staging) for the planned arena.
+void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
+    char *base = b->dmem;
+    int *err = (int *)(base + P.err);
+    SurfaceJob *sj = (SurfaceJob *)(b->host + P.jobs);
+    RequestJob *rj = (RequestJob *)(b->host + P.reqs);
+    for (size_t i = 0; i < P.surf.size(); ++i) {
+        const Surface &S = P.surf[i];
+        SurfaceJob J;
+        memset(&J, 0, sizeof(J));
+        J.fine = pass_args(S, base, err, false);
+        if (S.g.levels >= 3) J.coarse = pass_args(S, base, err, true);
+        J.stamp = (uint32_t *)(base + S.stamp);
+        J.fmask = S.foveated ? (uint8_t *)(base + S.fmask) : nullptr;
+        J.cls = S.cls;
+        int need = (J.fine.a_floats + J.fine.p_floats) * 4;
+        if (S.g.levels >= 3) need = std::max(need, (J.coarse.a_floats + J.coarse.p_floats) * 4);
+        P.smem[S.cls] = std::max(P.smem[S.cls], need);
+        memcpy(&sj[i], &J, sizeof(J));
+    }
+    for (int i = 0; i < n; ++i) {
+        const wv_request &r = reqs[i];
+        const Surface &S = P.surf[P.req_surface[i]];
+        RequestJob R;
+        memset(&R, 0, sizeof(R));
+        R.v = make_view(r.yaw, r.pitch, r.fov, r.out.width, r.out.height, S.g.p[0].w, S.g.p[0].h);
+        R.f = make_frustum(R.v);
+        R.fov.on = r.fovea;
+        R.fov.gx = r.gaze_x;
+        R.fov.gy = r.gaze_y;
+        R.fov.r1 = r.r1;
+        R.fov.r2 = r.r2;
+        R.surface = P.req_surface[i];
+        R.rs.v = R.v;
+        for (int p = 0; p < 3; ++p) {
+            const bool has = p < S.g.planes;
+            R.rs.plane[p] = has ? (const uint8_t *)(base + S.recon[p]) : nullptr;
+            R.rs.w[p] = has ? S.g.p[p].w : 0;
+            R.rs.h[p] = has ? S.g.p[p].h : 0;
+        }
+        R.rs.planes = S.g.planes;
+        R.rs.c420 = S.g.c420;
+        R.rs.uv = nullptr;
+        R.rs.out = (uint8_t *)r.out.dptr;
+        R.rs.pitch = r.out.pitch_bytes;
+        memcpy(&rj[i], &R, sizeof(R));
+    }
+}
+
+// Enqueue the six steps on cs (captured into a graph, or run directly).
+cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool timed) {
+    char *base = b->dmem;
+    const SurfaceJob *surfs = (const SurfaceJob *)(base + P.jobs);
+    const RequestJob *rq = (const RequestJob *)(base + P.reqs);
+    int *ctr = (int *)(base + P.ctr);
+    const int m = (int)P.surf.size();
+    cudaError_t e = cudaMemcpyAsync(base + P.jobs, b->host + P.jobs, P.job_bytes - P.jobs,
+                                    cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return e;
+    e = timed ? cudaEventRecord(b->staged, cs) : cudaEventRecordWithFlags(b->staged, cs, cudaEventRecordExternal);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(base + P.ctr, 0, P.clear_bytes, cs);
+    if (e != cudaSuccess) return e;
+    if (timed) cudaEventRecord(b->ev[0], cs);
+    launch_footprint_batch(rq, surfs, n, P.max_cx, P.max_cy, cs);
+    if (timed) cudaEventRecord(b->ev[1], cs);
+    BatchLists lists;
+    for (int c = 0; c < kClasses; ++c) {
+        lists.coarse[c] = (uint2 *)(base + P.lists_c[c]);
+        lists.fine[c] = (uint2 *)(base + P.lists_f[c]);
+    }
+    launch_select_batch(surfs, m, P.max_stamps, lists, ctr, cs);
+    if (timed) cudaEventRecord(b->ev[2], cs);
+    for (int c = 0; c < kClasses; ++c) {
+        if (!P.smem[c]) continue;
+        e = launch_decode_batch(c / (2 * kMaxBands), c % kMaxBands + 1, (c / kMaxBands) % 2 == 1, surfs,
+                                lists.coarse[c], lists.fine[c], ctr + 4 * c,
+                                ctr + kBatchCtr, (int *)(base + P.err), P.smem[c], cs);
+        if (e != cudaSuccess) return e;
+    }
+    if (timed) cudaEventRecord(b->ev[3], cs);
+    launch_resample_batch(rq, n, P.max_w, P.max_h, cs);
+    if (timed) cudaEventRecord(b->ev[4], cs);
+    return cudaGetLastError();
+}
+
+std::vector<long long> shape_key(const wv_batch *b, const Plan &P, int n) {
+    std::vector<long long> k = {n, (long long)P.surf.size(), (long long)(uintptr_t)b->dmem,
+                                (long long)(uintptr_t)b->host, (long long)P.job_bytes,
+                                (long long)P.clear_bytes, P.max_cx, P.max_cy, P.max_stamps,
+                                P.max_w, P.max_h};
+    for (int c = 0; c < kClasses; ++c) {
+        k.push_back(P.smem[c]);
+        k.push_back((long long)P.lists_c[c]);
+        k.push_back((long long)P.lists_f[c]);
+    }
+    return k;
+}
+
+int ensure_memory(wv_batch *b, const Plan &P) {
+    if (P.total > b->dbytes) {
+        if (b->launched) cudaEventSynchronize(b->done);
+        if (b->dmem) cudaFree(b->dmem);
+        b->dmem = nullptr;
+        b->dbytes = 0;
+        const size_t want = P.total + P.total / 4;
+        if (cudaMalloc((void **)&b->dmem, want) != cudaSuccess) {
+            cudaGetLastError();
+            return WV_ERR_OOM;
+        }
+        b->dbytes = want;
+        cudaMemset(b->dmem + P.err, 0, 64);
+    }
+    if (P.job_bytes > b->hbytes) {
+        if (b->launched) cudaEventSynchronize(b->done);
+        if (b->host) cudaFreeHost(b->host);
+        b->host = nullptr;
+        b->hbytes = 0;
+        const size_t want = P.job_bytes + P.job_bytes / 4;
+        if (cudaHostAlloc((void **)&b->host, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return WV_ERR_OOM;
+        }
+        b->hbytes = want;
+    }
+    return WV_OK;
+}
+
+int run_batch(wv_batch *b, const wv_request *reqs, int n, cudaStream_t cs) {
+    if (!b || n < 0 || (n > 0 && !reqs)) return WV_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const int rc = check_request(reqs[i]);
+        if (rc != WV_OK) return rc;
+    }
+    if (n == 0) return WV_OK;
+    Plan P;
+    int rc = plan_batch(b, reqs, n, P);
+    if (rc != WV_OK) return rc;
+    rc = ensure_memory(b, P);
+    if (rc != WV_OK) return rc;
+    // the previous launch must have consumed the staging before it is rewritten
+    if (b->launched) cudaEventSynchronize(b->staged);
+    fill_jobs(b, reqs, n, P);
+    // a launch on another CUDA stream than the previous one waits for it
+    if (b->launched && cs != b->cs) cudaStreamWaitEvent(cs, b->done, 0);
+    b->err = (int *)(b->dmem + P.err);
+    b->ctr_dev = (int *)(b->dmem + P.ctr);
+    b->n_ctr = P.n_ctr;
+    b->last_requests = n;
+    b->last_surfaces = (int)P.surf.size();
+    cudaError_t e;
+    if (b->use_graph && !b->timing) {
+        const std::vector<long long> key = shape_key(b, P, n);
+        if (!b->exec || key != b->shape) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = enqueue(b, P, n, b->cap, false);
+                e = cudaStreamEndCapture(b->cap, &graph);
+                if (e1 != cudaSuccess) e = e1;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b->exec = nullptr;
+                return WV_ERR_CUDA;
+            }
+            b->shape = key;
+        }
+        e = cudaGraphLaunch(b->exec, cs);
+    } else {
+        e = enqueue(b, P, n, cs, true);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return WV_ERR_CUDA;
+    }
+    b->cs = cs;
+    b->launched = true;
+    return WV_OK;
+}
+
+std::mutex g_default_mutex;
+std::map<int, wv_batch *> g_default;   // per device: the context of wv_decode_batch
+
+}  // namespace
+
+extern "C" {
+
+int wv_batch_create(void *cuda_stream, wv_batch **out) {
+    if (!out) return WV_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return WV_ERR_CUDA;
+    }
+    wv_batch *b = new (std::nothrow) wv_batch();
+    if (!b) return WV_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->cs = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        wv_batch_close(b);
+        return WV_ERR_CUDA;
+    }
+    *out = b;
+    return WV_OK;
+}
+
+void wv_batch_close(wv_batch *b) {
+    if (!b) return;
+    if (b->launched) cudaEventSynchronize(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->host) cudaFreeHost(b->host);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+int wv_batch_decode(wv_batch *b, const wv_request *reqs, int n) {
+    if (!b) return WV_ERR_ARG;
+    return run_batch(b, reqs, n, b->cs);
+}
+
+int wv_batch_set_cuda_stream(wv_batch *b, void *cuda_stream) {
+    if (!b) return WV_ERR_ARG;
+    if (b->launched && (cudaStream_t)cuda_stream != b->cs)
+        cudaStreamWaitEvent((cudaStream_t)cuda_stream, b->done, 0);
+    b->cs = (cudaStream_t)cuda_stream;
+    return WV_OK;
+}
+
+int wv_batch_device_bytes(wv_batch *b, const wv_request *reqs, int n, size_t *bytes) {
+    if (!b || !bytes || n < 0 || (n > 0 && !reqs)) return WV_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (check_request(reqs[i]) != WV_OK) return WV_ERR_ARG;
+    Plan P;
+    const int rc = plan_batch(b, reqs, n, P);
+    if (rc != WV_OK) return rc;
+    *bytes = P.total;
+    return WV_OK;
+}
+
+int wv_batch_sync_status(wv_batch *b) {
+    if (!b) return WV_ERR_ARG;
+    if (!b->launched) return WV_OK;
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return WV_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, b->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return WV_ERR_CUDA;
+    if (err) cudaMemset(b->err, 0, 4);
+    return err;
+}
+
+int wv_batch_stats(wv_batch *b, wv_batch_info *info) {
+    if (!b || !info) return WV_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    if (!b->launched) return WV_OK;
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return WV_ERR_CUDA;
+    std::vector<int> c(b->n_ctr);
+    if (cudaMemcpy(c.data(), b->ctr_dev, sizeof(int) * b->n_ctr, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return WV_ERR_CUDA;
+    info->requests = b->last_requests;
+    info->surfaces = b->last_surfaces;
+    for (int k = 0; k < kClasses; ++k) {
+        info->coarse_tiles += c[4 * k + 1];
+        info->fine_tiles += c[4 * k + 2];
+    }
+    info->bytes = b->dbytes;
+    if (b->timing) {
+        float ms = 0.f;
+        for (int i = 0; i < 4; ++i) {
+            cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]);
+            info->ms[i] = ms;
+        }
+    }
+    return WV_OK;
+}
+
+int wv_batch_set_timing(wv_batch *b, int on) {
+    if (!b || on < 0 || on > 1) return WV_ERR_ARG;
+    b->timing = on != 0;
+    return WV_OK;
+}
+
+int wv_batch_set_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height,
+                            int tile, int ctile) {
+    if (!b || (tile != 64 && tile != 128) || (ctile != 32 && ctile != 64)) return WV_ERR_ARG;
+    b->tuned[TuneKey{wavelet, levels, width, height}] = {tile, ctile};
+    return WV_OK;
+}
+
+int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile,
+                        int *ctile) {
+    if (!b || !tile || !ctile) return WV_ERR_ARG;
+    auto it = b->tuned.find(TuneKey{wavelet, levels, width, height});
+    *tile = it == b->tuned.end() ? kTile : it->second.first;
+    *ctile = it == b->tuned.end() ? kCoarseTile : it->second.second;
+    return WV_OK;
+}
+
+int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps) {
+    if (!b || n <= 0 || !reqs || reps < 1) return WV_ERR_ARG;
+    std::vector<TuneKey> keys;
+    for (int i = 0; i < n; ++i) {
+        if (check_request(reqs[i]) != WV_OK) return WV_ERR_ARG;
+        const Geom &g = reqs[i].s->g;
+        const TuneKey k{g.wavelet, g.levels, g.p[0].w, g.p[0].h};
+        if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+    }
+    const std::pair<int, int> cand[4] = {{128, 64}, {128, 32}, {64, 64}, {64, 32}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WV_ERR_CUDA;
+    int rc = WV_OK;
+    const bool timing = b->timing;
+    b->timing = false;
+    for (const TuneKey &k : keys) {
+        float best = 1e30f;
+        std::pair<int, int> pick = cand[0];
+        for (const auto &c : cand) {
+            b->tuned[k] = c;
+            rc = run_batch(b, reqs, n, b->cs);   // warm-up (captures the graph)
+            if (rc != WV_OK) break;
+            cudaEventRecord(e0, b->cs);
+            for (int r = 0; r < reps && rc == WV_OK; ++r) rc = run_batch(b, reqs, n, b->cs);
+            cudaEventRecord(e1, b->cs);
+            if (rc != WV_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = rc != WV_OK ? rc : WV_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+        b->tuned[k] = pick;
+        if (rc != WV_OK) break;
+    }
+    b->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int wv_decode_batch(const wv_request *reqs, int n, void *cuda_stream) {
+    if (n < 0 || (n > 0 && !reqs)) return WV_ERR_ARG;
+    if (n == 0) return WV_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return WV_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_default_mutex);
+    wv_batch *&b = g_default[dev];
+    if (!b) {
+        const int rc = wv_batch_create(cuda_stream, &b);
+        if (rc != WV_OK) {
+            b = nullptr;
+            return rc;
+        }
+    }
+    return run_batch(b, reqs, n, (cudaStream_t)cuda_stream);
+}
+
+void wv_release_default_batch(void) {
+    std::lock_guard<std::mutex> lock(g_default_mutex);
+    for (auto &kv : g_default) wv_batch_close(kv.second);
+    g_default.clear();
+}
+
+}  // extern "C"

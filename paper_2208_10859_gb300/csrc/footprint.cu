@@ -11,8 +11,22 @@ namespace wv {
 
 namespace {
 
+// Coarse tiles [c_lo, c_hi] (ctile samples of LL_2) holding LL_2 indices
+// [lo, hi] of a subband of n2 samples after whole-sample symmetric extension.
+// A tile t of side T needs the LL_2 window [q t - 3, q t + q + 2] (q = T / 4;
+// 9/7 halo, the 5/3 window is narrower).
+__device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int ctile, int &c_lo,
+                                            int &c_hi) {
+    int a = max(lo, 0), b = min(hi, n2 - 1);
+    if (lo < 0) b = max(b, min(-lo, n2 - 1));
+    if (hi > n2 - 1) a = min(a, max(2 * (n2 - 1) - hi, 0));
+    c_lo = a / ctile;
+    c_hi = b / ctile;
+}
 
-// One thread per mask cell.  The viewport samples the frame at positions
+constexpr float kReach = 3.0f;
+
+// Footprint: one thread per mask cell.  The viewport samples the frame at positions
 // inside the image of its frustum; every bilinear tap (luma, and centre-sited
 // chroma mapped to luma) lies within 2.5 luma pixels of its position.  A cell
 // is therefore needed when the cell grown by kReach pixels on every side
@@ -26,28 +40,8 @@ namespace {
 // the frustum, so the mask is a superset of the needed cells (cells near the
 // frustum's corners may be included without being needed).  Rows 0 and
 // H/32 - 1 extend to the poles because the resampler clamps v to the frame.
-// Coarse tiles [c_lo, c_hi] (kCoarseTile samples of LL_2) holding LL_2
-// indices [lo, hi] of a subband of n2 samples after whole-sample symmetric
-// extension.  A tile t needs the LL_2 window [q t - 3, q t + q + 2]
-// (q = kTile / 4; 9/7 halo, the 5/3 window is narrower).
-__device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int &c_lo, int &c_hi) {
-    int a = max(lo, 0), b = min(hi, n2 - 1);
-    if (lo < 0) b = max(b, min(-lo, n2 - 1));
-    if (hi > n2 - 1) a = min(a, max(2 * (n2 - 1) - hi, 0));
-    c_lo = a / kCoarseTile;
-    c_hi = b / kCoarseTile;
-}
-
-constexpr float kReach = 3.0f;
-
-__global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mask,
-                            uint32_t *__restrict__ tile_gen, uint32_t *__restrict__ ctile_gen,
-                            uint32_t gen, int *counters) {
-    const int cells_x = g.cells_x, cells_y = g.cells_y, eq_w = g.p[0].w, eq_h = g.p[0].h;
-    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (cx == 0 && cy == 0) counters[0] = counters[1] = 0;   // tile counts of this viewport
-    if (cx >= cells_x || cy >= cells_y) return;
+__device__ __forceinline__ bool cell_needed(const Frustum &f, int eq_w, int eq_h, int cells_y,
+                                            int cx, int cy) {
     // grown cell in pixel coordinates -> longitude / latitude (radians / pi)
     const float u0 = (float)(cx * kCell) - kReach, u1 = (float)((cx + 1) * kCell) + kReach;
     const float v0 = (float)(cy * kCell) - kReach, v1 = (float)((cy + 1) * kCell) + kReach;
@@ -82,36 +76,98 @@ __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mas
     mincos = fminf(fmaxf(mincos, -1.0f), 1.0f);
     // sin(rho), with slack for float rounding of the dot products
     const float srho = sqrtf(fmaxf(0.0f, 1.0f - mincos * mincos)) * 1.01f + 1e-5f;
-    bool hit = mincos > -0.5f;   // caps wider than 120 degrees: always keep
-    if (hit) {
+    if (mincos <= -0.5f) return true;   // caps wider than 120 degrees: always keep
+    bool hit = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float d = f.n[k][0] * c[0] + f.n[k][1] * c[1] + f.n[k][2] * c[2];
-            hit = hit && (d >= -srho);
-        }
-    } else {
-        hit = true;
+    for (int k = 0; k < 4; ++k) {
+        const float d = f.n[k][0] * c[0] + f.n[k][1] * c[1] + f.n[k][2] * c[2];
+        hit = hit && (d >= -srho);
     }
-    mask[cy * cells_x + cx] = hit ? 1 : 0;
-    if (hit) {   // stamp the tile of every plane that holds this cell, and its coarse tiles
-        int base = 0, cbase = 0;
-        for (int p = 0; p < g.planes; ++p) {
-            const PlaneGeom &pg = g.p[p];
-            const int sh = (pg.sub == 2) ? 3 : 2;   // cells per tile side: 4 (or 8 at half size)
-            const int tx = cx >> sh, ty = cy >> sh;
-            tile_gen[base + ty * pg.tiles_x + tx] = gen;
-            if (pg.ctiles_x > 0) {
-                int cx0, cx1, cy0, cy1;
-                const int q = kTile / 4;   // LL_2 samples per tile side
-                coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, cx0, cx1);
-                coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, cy0, cy1);
-                for (int y = cy0; y <= cy1; ++y)
-                    for (int x = cx0; x <= cx1; ++x) ctile_gen[cbase + y * pg.ctiles_x + x] = gen;
-            }
-            base += pg.tiles_x * pg.tiles_y;
-            cbase += pg.ctiles_x * pg.ctiles_y;
+    return hit;
+}
+
+// Stamp the tile of every plane that holds cell (cx, cy), and the coarse
+// tiles that tile reads.
+__device__ __forceinline__ void stamp_cell(const Geom &g, int cx, int cy, uint32_t *tile_gen,
+                                           uint32_t *ctile_gen, uint32_t gen) {
+    int base = 0, cbase = 0;
+    for (int p = 0; p < g.planes; ++p) {
+        const PlaneGeom &pg = g.p[p];
+        const int tx = cx >> pg.tile_shift, ty = cy >> pg.tile_shift;
+        tile_gen[base + ty * pg.tiles_x + tx] = gen;
+        if (pg.ctiles_x > 0) {
+            int cx0, cx1, cy0, cy1;
+            const int q = g.tile / 4;   // LL_2 samples per tile side
+            coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, g.ctile, cx0, cx1);
+            coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, g.ctile, cy0, cy1);
+            for (int y = cy0; y <= cy1; ++y)
+                for (int x = cx0; x <= cx1; ++x) ctile_gen[cbase + y * pg.ctiles_x + x] = gen;
         }
+        base += pg.tiles_x * pg.tiles_y;
+        cbase += pg.ctiles_x * pg.ctiles_y;
     }
+}
+
+// Foveation bits of cell (cx, cy): bit 0 = level-1 details kept (centre
+// within r1 of the gaze), bit 1 = level-2 details kept (within r2).  The
+// centre direction is rotated into viewer coordinates by R^T.
+__device__ __forceinline__ uint8_t fovea_bits(const View &v, const Fovea &fv, int eq_w, int eq_h,
+                                              int cx, int cy) {
+    const float lon = fmaf((float)(cx * kCell + kCell / 2), 2.0f / (float)eq_w, -1.0f);
+    const float lat = fmaf(-(float)(cy * kCell + kCell / 2), 1.0f / (float)eq_h, 0.5f);
+    float sl, cl, sp, cp;
+    sincospif(lon, &sl, &cl);
+    sincospif(lat, &sp, &cp);
+    const float dx = cp * sl, dy = sp, dz = cp * cl;
+    const float x = v.r[0] * dx + v.r[3] * dy + v.r[6] * dz;
+    const float y = v.r[1] * dx + v.r[4] * dy + v.r[7] * dz;
+    const float z = v.r[2] * dx + v.r[5] * dy + v.r[8] * dz;
+    if (!(z > 0.0f)) return 0;
+    const float d = fmaxf(fabsf(atan2f(x, z) - fv.gx), fabsf(atan2f(y, z) - fv.gy));
+    return (uint8_t)((d <= fv.r1 ? 1 : 0) | (d <= fv.r2 ? 2 : 0));
+}
+
+__global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mask,
+                            uint32_t *__restrict__ tile_gen, uint32_t *__restrict__ ctile_gen,
+                            uint32_t gen, int *counters) {
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx == 0 && cy == 0) counters[0] = counters[1] = 0;   // tile counts of this viewport
+    if (cx >= g.cells_x || cy >= g.cells_y) return;
+    const bool hit = cell_needed(f, g.p[0].w, g.p[0].h, g.cells_y, cx, cy);
+    mask[cy * g.cells_x + cx] = hit ? 1 : 0;
+    if (hit) stamp_cell(g, cx, cy, tile_gen, ctile_gen, gen);
+}
+
+// Batch: one z-slice of the grid per request; stamps go to the request's
+// surface (stamp arrays cleared before the launch, stamp value 1).
+__global__ void k_footprint_batch(const RequestJob *__restrict__ reqs,
+                                  const SurfaceJob *__restrict__ surfs) {
+    const RequestJob &r = reqs[blockIdx.z];
+    const SurfaceJob &s = surfs[r.surface];
+    const Geom &g = s.fine.g;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx >= g.cells_x || cy >= g.cells_y) return;
+    if (cell_needed(r.f, g.p[0].w, g.p[0].h, g.cells_y, cx, cy))
+        stamp_cell(g, cx, cy, s.stamp, s.stamp + g.total_tiles, 1u);
+    if (r.fov.on && s.fmask)
+        s.fmask[cy * g.cells_x + cx] = fovea_bits(r.v, r.fov, g.p[0].w, g.p[0].h, cx, cy);
+}
+
+// Tile entry: plane << 28 | ty << 14 | tx, from index t of the plane-ordered
+// tile (or coarse tile) range of a geometry.
+__device__ __forceinline__ uint32_t tile_entry(const Geom &g, int t, bool coarse) {
+    int plane = 0;
+    for (;;) {
+        const PlaneGeom &pg = g.p[plane];
+        const int n = coarse ? pg.ctiles_x * pg.ctiles_y : pg.tiles_x * pg.tiles_y;
+        if (t < n || plane == g.planes - 1) break;
+        t -= n;
+        ++plane;
+    }
+    const int nx = coarse ? g.p[plane].ctiles_x : g.p[plane].tiles_x;
+    return ((uint32_t)plane << 28) | ((uint32_t)(t / nx) << 14) | (uint32_t)(t % nx);
 }
 
 // Tile selection: one thread per tile and one per coarse tile of every
@@ -137,22 +193,42 @@ __global__ void k_select_tiles(Geom g, const uint32_t *__restrict__ tile_gen,
     const int t0 = coarse ? tid - g.total_tiles : tid;
     const bool valid = coarse ? t0 < g.total_ctiles : true;
     bool sel = valid && (coarse ? ctile_gen[t0] : tile_gen[t0]) == gen;
-    uint32_t entry = 0;
-    if (sel) {
-        int plane = 0, t = t0;
-        for (;;) {
-            const PlaneGeom &pg = g.p[plane];
-            const int n = coarse ? pg.ctiles_x * pg.ctiles_y : pg.tiles_x * pg.tiles_y;
-            if (t < n || plane == g.planes - 1) break;
-            t -= n;
-            ++plane;
-        }
-        const int nx = coarse ? g.p[plane].ctiles_x : g.p[plane].tiles_x;
-        entry = ((uint32_t)plane << 28) | ((uint32_t)(t / nx) << 14) | (uint32_t)(t % nx);
-    }
+    const uint32_t entry = sel ? tile_entry(g, t0, coarse) : 0u;
     // warps straddling the two ranges: both calls are made by all lanes
     append(sel && !coarse, entry, tiles, &counters[0]);
     append(sel && coarse, entry, ctiles, &counters[1]);
+}
+
+__device__ __forceinline__ void append2(bool sel, uint2 entry, uint2 *list, int *count) {
+    const unsigned ballot = __ballot_sync(0xffffffffu, sel);
+    if (!sel) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(ballot));
+    base = __shfl_sync(ballot, base, leader);
+    list[base + __popc(ballot & ((1u << lane) - 1u))] = entry;
+}
+
+// Batch selection: row blockIdx.y of the grid covers the stamps of surface
+// blockIdx.y; listed entries carry the surface index.  Coarse tiles are also
+// counted per surface (the fine tiles of a surface wait for that many).
+__global__ void k_select_batch(const SurfaceJob *__restrict__ surfs, BatchLists lists, int *ctr) {
+    const int si = blockIdx.y;
+    const SurfaceJob &s = surfs[si];
+    const Geom &g = s.fine.g;
+    const int total = g.total_tiles + g.total_ctiles;
+    if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block outside: uniform
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool is_coarse = tid >= g.total_tiles;
+    const bool sel = tid < total && s.stamp[tid] != 0;
+    uint2 e = make_uint2((uint32_t)si, 0u);
+    if (sel) e.y = tile_entry(g, is_coarse ? tid - g.total_tiles : tid, is_coarse);
+    const int c = s.cls;
+    append2(sel && !is_coarse, e, lists.fine[c], &ctr[4 * c + 2]);
+    const unsigned cb = __ballot_sync(0xffffffffu, sel && is_coarse);
+    if (cb && (threadIdx.x & 31) == __ffs(cb) - 1) atomicAdd(&ctr[kBatchCtr + 2 * si], __popc(cb));
+    append2(sel && is_coarse, e, lists.coarse[c], &ctr[4 * c + 1]);
 }
 
 __global__ void k_all_tiles(int plane, int tiles_x, int tiles_y, uint32_t *tiles,
@@ -181,6 +257,19 @@ void launch_footprint(const Geom &g, const View &v, uint8_t *mask, uint32_t *til
     dim3 block(32, 8);
     dim3 grid((g.cells_x + 31) / 32, (g.cells_y + 7) / 8);
     k_footprint<<<grid, block, 0, cs>>>(v, f, g, mask, tile_gen, ctile_gen, gen, counters);
+}
+
+void launch_footprint_batch(const RequestJob *reqs, const SurfaceJob *surfs, int n, int max_cx,
+                            int max_cy, cudaStream_t cs) {
+    dim3 block(32, 8);
+    dim3 grid((max_cx + 31) / 32, (max_cy + 7) / 8, n);
+    k_footprint_batch<<<grid, block, 0, cs>>>(reqs, surfs);
+}
+
+void launch_select_batch(const SurfaceJob *surfs, int m, int max_stamps, const BatchLists &lists,
+                         int *ctr, cudaStream_t cs) {
+    dim3 grid((max_stamps + 255) / 256, m);
+    k_select_batch<<<grid, 256, 0, cs>>>(surfs, lists, ctr);
 }
 
 void launch_select_tiles(const Geom &g, const uint32_t *tile_gen, const uint32_t *ctile_gen,

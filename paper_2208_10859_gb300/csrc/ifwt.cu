@@ -61,39 +61,6 @@ struct Traits<1> {   // CDF 9/7, float lifting
     static constexpr int V = 4;
 };
 
-struct TileArgs {
-    Geom g;
-    const int16_t *payload;
-    const int32_t *table;
-    Bands bands;
-    int l_top, l_bot;        // levels synthesised: l_top down to l_bot
-    int tile;                // output tile side at level l_bot - 1
-    const float *ll_in[3];   // LL_{l_top} planes when l_top < levels
-    int ll_in_pitch[3];
-    uint8_t *out_u8[3];      // l_bot == 1: samples
-    float *out_f32;          // l_bot == 1: float samples of plane f32_plane
-    int f32_plane;
-    float *ll_out[3];        // l_bot > 1: LL_{l_bot - 1} planes
-    int ll_out_pitch[3];
-    const uint32_t *tiles;   // tile list (count entries)
-    const int *count;
-    int *err;
-    int a_floats, p_floats;
-    // 9/7: half the dequantisation step times the synthesis band scaling
-    // folded over all levels.  Synthesis scales a low band by K and a high
-    // band by 1/K per axis at every level, the LL produced by level l + 1
-    // included; with LL_L x K^(2L), HL_l and LH_l x K^(2(l-1)), HH_l x
-    // K^(2(l-2)) the output of level l carries K^(2(l-1)), exactly the factor
-    // the next finer level expects of its LL, and level 1 returns unscaled
-    // samples.  (The half: the midpoint reconstruction is computed as
-    // (2q + sign q) step / 2.)
-    float scale[kMaxLevels + 1][4];
-};
-
-struct Range {
-    int lo, hi;
-};
-
 __device__ __host__ __forceinline__ int floor8(int x) { return x & ~7; }
 
 // Index of coefficient k of a subband of n coefficients after whole-sample
@@ -155,6 +122,7 @@ template <int NB>
 struct Raw {
     uint4 q[2][NB];      // [even/odd columns][band]
     bool have[2][NB];
+    int keep[2];         // foveation: bit 0 keeps coefficients 0-3, bit 1 keeps 4-7
 };
 
 template <int WAV, int NB>
@@ -207,11 +175,22 @@ __device__ __forceinline__ void combine8(const TileArgs &a, const uint4 *q, cons
     }
 }
 
+// Foveated decoding (Sec. 3.7): whether the level-l (l = 1, 2) detail
+// coefficient (kx, ky) of a plane is kept, from the foveation bits of the
+// mask cell holding its nominal luma position (kx 2^l sub, ky 2^l sub).
+__device__ __forceinline__ bool fovea_kept(const TileArgs &a, const PlaneGeom &pg, int l, int kx,
+                                           int ky) {
+    const int X = (kx << l) * pg.sub, Y = (ky << l) * pg.sub;
+    return (__ldg(&a.fmask[(Y >> kLogCell) * a.g.cells_x + (X >> kLogCell)]) >> (l - 1)) & 1;
+}
+
 // Dequantised, rebuilt coefficient (scalar path for edge chunks).
-template <int WAV, int NB>
+template <int WAV, int NB, bool FOV>
 __device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, const PlaneGeom &pg,
                                                          int level, int sub, int kx, int ky) {
     const Geom &g = a.g;
+    using T = typename Traits<WAV>::T;
+    if (FOV && level <= 2 && sub != 0 && !fovea_kept(a, pg, level, kx, ky)) return T(0);
     const int lb = g.log2b, bm = g.block - 1;
     const int bid = pg.base[level][sub] + (ky >> lb) * pg.nbx[level] + (kx >> lb);
     const size_t off = (size_t)((ky & bm) << lb) + (kx & bm);
@@ -257,7 +236,7 @@ struct Task {
     bool fast;           // chunk entirely inside the subband (no extension)
 };
 
-template <int WAV, int NB>
+template <int WAV, int NB, bool FOV>
 __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg, const LevelGeo &G,
                                           const Task &t, Raw<NB> &r) {
     const Geom &g = a.g;
@@ -272,13 +251,19 @@ __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg
             r.have[e][b] = false;
             r.q[e][b] = make_uint4(0, 0, 0, 0);
         }
+        r.keep[e] = 3;
         if (!t.active || !t.fast || (sub == 0 && G.l < g.levels)) continue;
+        // foveation: coefficients 0-3 and 4-7 of the chunk (one or two cells);
+        // a chunk that keeps nothing is not loaded, a half is cleared later
+        if (FOV && G.l <= 2 && sub != 0)
+            r.keep[e] = (int)fovea_kept(a, pg, G.l, kx, t.ky) | ((int)fovea_kept(a, pg, G.l, kx + 4, t.ky) << 1);
+        const bool any = !FOV || r.keep[e] != 0;
         const int bid = pg.base[G.l][sub] + (t.ky >> lb) * pg.nbx[G.l] + (kx >> lb);
         const size_t off = (size_t)((t.ky & bm) << lb) + (kx & bm);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-            if (slot >= 0) {
+            if (slot >= 0 && any) {
                 r.have[e][b] = true;
                 r.q[e][b] = __ldg(reinterpret_cast<const uint4 *>(a.payload + (size_t)slot * bsz + off));
             }
@@ -286,9 +271,19 @@ __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg
     }
 }
 
-template <int WAV, int NB>
+// Foveation: clear coefficients 0-3 (keep bit 0 unset) or 4-7 (bit 1 unset).
+template <int NB>
+__device__ __forceinline__ void clear_halves(uint4 (&q)[NB], int keep) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        if (!(keep & 1)) q[b].x = q[b].y = 0u;
+        if (!(keep & 2)) q[b].z = q[b].w = 0u;
+    }
+}
+
+template <int WAV, int NB, bool FOV>
 __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &pg, int plane,
-                                            const LevelGeo &G, const Task &t, const Raw<NB> &r,
+                                            const LevelGeo &G, const Task &t, Raw<NB> &r,
                                             const float *P, int nch, float *A) {
     using T = typename Traits<WAV>::T;
     const Geom &g = a.g;
@@ -300,32 +295,36 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
         T ev[8], od[8];
         // odd columns: HL (even row) or HH (odd row)
         if (t.fast) {
+            if (FOV && r.keep[1] != 3) clear_halves<NB>(r.q[1], r.keep[1]);
             combine8<WAV, NB>(a, r.q[1], r.have[1], a.scale[G.l][s_odd], od);
         } else {
 #pragma unroll
             for (int m = 0; m < 8; ++m)
-                od[m] = coef1<WAV, NB>(a, pg, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
+                od[m] = coef1<WAV, NB, FOV>(a, pg, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
         }
         // even columns: LH (odd row) or LL (even row)
         if (s_even == 2 || G.l == g.levels) {
             if (t.fast) {
+                if (FOV && r.keep[0] != 3) clear_halves<NB>(r.q[0], r.keep[0]);
                 combine8<WAV, NB>(a, r.q[0], r.have[0], a.scale[G.l][s_even], ev);
             } else {
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
-                    ev[m] = coef1<WAV, NB>(a, pg, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
+                    ev[m] = coef1<WAV, NB, FOV>(a, pg, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
             }
         } else if (G.l == a.l_top) {   // LL from a plane written by a coarser pass
             const float *src = a.ll_in[plane] + (size_t)t.ky * a.ll_in_pitch[plane];
             if (t.fast) {
-                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src + kx));
-                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src + kx + 4));
+                // L2 loads: in a batch the coarse pass writing these planes
+                // runs in the same launch
+                const float4 x0 = __ldcg(reinterpret_cast<const float4 *>(src + kx));
+                const float4 x1 = __ldcg(reinterpret_cast<const float4 *>(src + kx + 4));
                 const float f[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
                 for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(f[m]);
             } else {
 #pragma unroll
-                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(src[refl_sub(kx + m, G.nw, 0)]);
+                for (int m = 0; m < 8; ++m) ev[m] = from_bits<T>(__ldcg(src + refl_sub(kx + m, G.nw, 0)));
             }
         } else {                       // LL from the level above (shared P)
             const int sp = 8 * G.nch;
@@ -405,7 +404,7 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
     }
 }
 
-template <int WAV, int NB>
+template <int WAV, int NB, bool FOV>
 __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &pg, int plane, const LevelGeo &G,
                             const float *P, float *A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -434,10 +433,10 @@ __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &
         const Task t0 = make(base + r_in);
         const Task t1 = make(base + stride + r_in);
         Raw<NB> r0, r1;
-        load_task<WAV, NB>(a, pg, G, t0, r0);
-        load_task<WAV, NB>(a, pg, G, t1, r1);
-        finish_task<WAV, NB>(a, pg, plane, G, t0, r0, P, nch, A);
-        finish_task<WAV, NB>(a, pg, plane, G, t1, r1, P, nch, A);
+        load_task<WAV, NB, FOV>(a, pg, G, t0, r0);
+        load_task<WAV, NB, FOV>(a, pg, G, t1, r1);
+        finish_task<WAV, NB, FOV>(a, pg, plane, G, t0, r0, P, nch, A);
+        finish_task<WAV, NB, FOV>(a, pg, plane, G, t1, r1, P, nch, A);
     }
 }
 
@@ -593,132 +592,203 @@ __device__ __forceinline__ void column_pair(const float *A, int sa, int col, int
     }
 }
 
-template <int WAV, int NB>
-__global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
+// Decode one tile (entry: plane << 28 | ty << 14 | tx) of a pass: levels
+// l_top down to l_bot; A and P are the CTA's shared arrays.
+template <int WAV, int NB, bool FOV>
+__device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float *A, float *P) {
     constexpr int H = Traits<WAV>::H;
-    extern __shared__ __align__(16) float smem[];
-    float *A = smem;
-    float *P = smem + a.a_floats;
     const Geom &g = a.g;
-    const int count = *(volatile const int *)a.count;
-
-    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) {
-        const uint32_t e = a.tiles[ti];
-        const int plane = (int)(e >> 28);
-        const int ty = (int)((e >> 14) & 0x3fff), tx = (int)(e & 0x3fff);
-        const PlaneGeom &pg = g.p[plane];
-        const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
-        // output ranges of every level (level l - 1 coordinates), l_bot upward
-        Range ox[kMaxLevels + 2], oy[kMaxLevels + 2];
-        ox[a.l_bot] = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
-        oy[a.l_bot] = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
-        for (int l = a.l_bot + 1; l <= a.l_top; ++l) {
-            ox[l] = {(ox[l - 1].lo >> 1) - H, (ox[l - 1].hi >> 1) + H};
-            oy[l] = {(oy[l - 1].lo >> 1) - H, (oy[l - 1].hi >> 1) + H};
+    const int plane = (int)(e >> 28);
+    const int ty = (int)((e >> 14) & 0x3fff), tx = (int)(e & 0x3fff);
+    const PlaneGeom &pg = g.p[plane];
+    const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
+    // output ranges of every level (level l - 1 coordinates), l_bot upward
+    Range ox[kMaxLevels + 2], oy[kMaxLevels + 2];
+    ox[a.l_bot] = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
+    oy[a.l_bot] = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
+    for (int l = a.l_bot + 1; l <= a.l_top; ++l) {
+        ox[l] = {(ox[l - 1].lo >> 1) - H, (ox[l - 1].hi >> 1) + H};
+        oy[l] = {(oy[l - 1].lo >> 1) - H, (oy[l - 1].hi >> 1) + H};
+    }
+    for (int l = a.l_top; l >= a.l_bot; --l) {
+        const LevelGeo G = make_level<H>(l, ox[l], oy[l], pg.w, pg.h);
+        const PLayout pn = p_layout(G.ox);   // next level's LL window in P
+        const bool fits = G.rows * G.sa <= a.a_floats && G.nch <= 32 &&
+                          (l == a.l_bot || (G.oy.hi - G.oy.lo + 1) * pn.stride <= a.p_floats);
+        if (!fits) {   // never taken for the sizes the launcher computed
+            if (threadIdx.x == 0) record_error(a.err, WV_ERR_DEVICE);
+            return;
         }
-        for (int l = a.l_top; l >= a.l_bot; --l) {
-            const LevelGeo G = make_level<H>(l, ox[l], oy[l], pg.w, pg.h);
-            const PLayout pn = p_layout(G.ox);   // next level's LL window in P
-            const bool fits = G.rows * G.sa <= a.a_floats && G.nch <= 32 &&
-                              (l == a.l_bot || (G.oy.hi - G.oy.lo + 1) * pn.stride <= a.p_floats);
-            if (!fits) {   // never taken for the sizes the launcher computed
-                if (threadIdx.x == 0) record_error(a.err, WV_ERR_DEVICE);
-                break;
-            }
-            // 1. gather + horizontal synthesis into A
-            gather_rows<WAV, NB>(a, pg, plane, G, P, A);
-            __syncthreads();
-            // 2. vertical synthesis of the columns the outputs need
-            const int nv = G.ox.hi - G.ox.lo + 1;
-            const int r0 = G.oy.lo - 2 * G.ky.lo, r1 = G.oy.hi - 2 * G.ky.lo + 1;
-            const int jc0 = G.ox.lo - 2 * G.kx0 - G.ja4;   // A column of output ox.lo (unswizzled)
-            if ((jc0 & 1) == 0 && (nv & 1) == 0) {
-                // column pairs: both columns of a pair sit in one 8-byte slot of
-                // the swizzled row (swz keeps j and j + 1 together for even j)
-                const int np = nv / 2;
-                const int nseg = max(1, min((int)blockDim.x / np, (r1 - r0) / 16));
-                const int items = np * nseg;
-                for (int it = threadIdx.x; it < items; it += blockDim.x) {
-                    const int jp = it % np, sg = it / np;
-                    const int ra = r0 + (r1 - r0) * sg / nseg, rb = r0 + (r1 - r0) * (sg + 1) / nseg;
-                    const int x = G.ox.lo + 2 * jp;
-                    const int col = swz(jc0 + 2 * jp);
-                    if (l > a.l_bot) {
-                        float *dst = P + (x - pn.col0);
-                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
-                            float *d = dst + (2 * G.ky.lo + i - G.oy.lo) * pn.stride;
-                            d[0] = v0;
-                            d[1] = v1;
-                        });
-                    } else if (a.l_bot > 1) {
-                        float *dst = a.ll_out[plane] + x;
-                        const int pitch = a.ll_out_pitch[plane];
-                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
-                            float *d = dst + (size_t)(2 * G.ky.lo + i) * pitch;
-                            d[0] = v0;
-                            d[1] = v1;
-                        });
-                    } else if (a.out_f32 && plane == a.f32_plane) {
-                        float *o = a.out_f32 + x;
-                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
-                            float *d = o + (size_t)(2 * G.ky.lo + i) * pg.w;
-                            d[0] = ((WAV == 1) ? v0 : (float)__float_as_int(v0)) + 128.0f;
-                            d[1] = ((WAV == 1) ? v1 : (float)__float_as_int(v1)) + 128.0f;
-                        });
-                    } else {
-                        uint8_t *o = a.out_u8[plane] + x;
-                        column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
-                            int p0, p1;
-                            if constexpr (WAV == 1) {
-                                p0 = __float2int_rd(v0 + 128.5f);
-                                p1 = __float2int_rd(v1 + 128.5f);
-                            } else {
-                                p0 = __float_as_int(v0) + 128;
-                                p1 = __float_as_int(v1) + 128;
-                            }
-                            const unsigned short w = (unsigned short)(min(max(p0, 0), 255) |
-                                                                      (min(max(p1, 0), 255) << 8));
-                            *reinterpret_cast<unsigned short *>(o + (size_t)(2 * G.ky.lo + i) * pg.w) = w;
-                        });
-                    }
-                }
-            } else {
-            const int nseg = max(1, min((int)blockDim.x / nv, (r1 - r0) / 16));
-            const int items = nv * nseg;
+        // 1. gather + horizontal synthesis into A
+        gather_rows<WAV, NB, FOV>(a, pg, plane, G, P, A);
+        __syncthreads();
+        // 2. vertical synthesis of the columns the outputs need
+        const int nv = G.ox.hi - G.ox.lo + 1;
+        const int r0 = G.oy.lo - 2 * G.ky.lo, r1 = G.oy.hi - 2 * G.ky.lo + 1;
+        const int jc0 = G.ox.lo - 2 * G.kx0 - G.ja4;   // A column of output ox.lo (unswizzled)
+        if ((jc0 & 1) == 0 && (nv & 1) == 0) {
+            // column pairs: both columns of a pair sit in one 8-byte slot of
+            // the swizzled row (swz keeps j and j + 1 together for even j)
+            const int np = nv / 2;
+            const int nseg = max(1, min((int)blockDim.x / np, (r1 - r0) / 16));
+            const int items = np * nseg;
             for (int it = threadIdx.x; it < items; it += blockDim.x) {
-                const int jj = it % nv, sg = it / nv;
+                const int jp = it % np, sg = it / np;
                 const int ra = r0 + (r1 - r0) * sg / nseg, rb = r0 + (r1 - r0) * (sg + 1) / nseg;
-                const int x = G.ox.lo + jj;
+                const int x = G.ox.lo + 2 * jp;
+                const int col = swz(jc0 + 2 * jp);
                 if (l > a.l_bot) {
                     float *dst = P + (x - pn.col0);
-                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
-                        dst[(2 * G.ky.lo + i - G.oy.lo) * pn.stride] = v;
+                    column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                        float *d = dst + (2 * G.ky.lo + i - G.oy.lo) * pn.stride;
+                        d[0] = v0;
+                        d[1] = v1;
                     });
                 } else if (a.l_bot > 1) {
                     float *dst = a.ll_out[plane] + x;
                     const int pitch = a.ll_out_pitch[plane];
-                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
-                        dst[(size_t)(2 * G.ky.lo + i) * pitch] = v;
+                    column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                        float *d = dst + (size_t)(2 * G.ky.lo + i) * pitch;
+                        d[0] = v0;
+                        d[1] = v1;
                     });
                 } else if (a.out_f32 && plane == a.f32_plane) {
                     float *o = a.out_f32 + x;
-                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
-                        const float f = (WAV == 1) ? v : (float)__float_as_int(v);
-                        o[(size_t)(2 * G.ky.lo + i) * pg.w] = f + 128.0f;
+                    column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                        float *d = o + (size_t)(2 * G.ky.lo + i) * pg.w;
+                        d[0] = ((WAV == 1) ? v0 : (float)__float_as_int(v0)) + 128.0f;
+                        d[1] = ((WAV == 1) ? v1 : (float)__float_as_int(v1)) + 128.0f;
                     });
                 } else {
                     uint8_t *o = a.out_u8[plane] + x;
-                    column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
-                        int p;
-                        if constexpr (WAV == 1) p = __float2int_rd(v + 128.5f);
-                        else p = __float_as_int(v) + 128;
-                        o[(size_t)(2 * G.ky.lo + i) * pg.w] = (uint8_t)min(max(p, 0), 255);
+                    column_pair<WAV>(A, G.sa, col, G.rows, ra, rb, [&](int i, float v0, float v1) {
+                        int p0, p1;
+                        if constexpr (WAV == 1) {
+                            p0 = __float2int_rd(v0 + 128.5f);
+                            p1 = __float2int_rd(v1 + 128.5f);
+                        } else {
+                            p0 = __float_as_int(v0) + 128;
+                            p1 = __float_as_int(v1) + 128;
+                        }
+                        const unsigned short w = (unsigned short)(min(max(p0, 0), 255) |
+                                                                  (min(max(p1, 0), 255) << 8));
+                        *reinterpret_cast<unsigned short *>(o + (size_t)(2 * G.ky.lo + i) * pg.w) = w;
                     });
                 }
             }
+        } else {
+        const int nseg = max(1, min((int)blockDim.x / nv, (r1 - r0) / 16));
+        const int items = nv * nseg;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int jj = it % nv, sg = it / nv;
+            const int ra = r0 + (r1 - r0) * sg / nseg, rb = r0 + (r1 - r0) * (sg + 1) / nseg;
+            const int x = G.ox.lo + jj;
+            if (l > a.l_bot) {
+                float *dst = P + (x - pn.col0);
+                column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                    dst[(2 * G.ky.lo + i - G.oy.lo) * pn.stride] = v;
+                });
+            } else if (a.l_bot > 1) {
+                float *dst = a.ll_out[plane] + x;
+                const int pitch = a.ll_out_pitch[plane];
+                column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                    dst[(size_t)(2 * G.ky.lo + i) * pitch] = v;
+                });
+            } else if (a.out_f32 && plane == a.f32_plane) {
+                float *o = a.out_f32 + x;
+                column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                    const float f = (WAV == 1) ? v : (float)__float_as_int(v);
+                    o[(size_t)(2 * G.ky.lo + i) * pg.w] = f + 128.0f;
+                });
+            } else {
+                uint8_t *o = a.out_u8[plane] + x;
+                column_segment<WAV>(A, G.sa, swz(jc0 + jj), G.rows, ra, rb, [&](int i, float v) {
+                    int p;
+                    if constexpr (WAV == 1) p = __float2int_rd(v + 128.5f);
+                    else p = __float_as_int(v) + 128;
+                    o[(size_t)(2 * G.ky.lo + i) * pg.w] = (uint8_t)min(max(p, 0), 255);
+                });
             }
-            __syncthreads();
         }
+        }
+        __syncthreads();
+    }
+}
+
+template <int WAV, int NB>
+__global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    float *A = smem;
+    float *P = smem + a.a_floats;
+    const int count = *(volatile const int *)a.count;
+    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) decode_one<WAV, NB, false>(a, a.tiles[ti], A, P);
+}
+
+// ---- batched decode: one persistent launch over all surfaces ---------------
+//
+// Work items are dispensed in order by one atomic counter: first every coarse
+// tile of every surface, then every fine tile.  A fine tile waits (thread 0,
+// bounded) until all coarse tiles of its surface are finished.  No wait can
+// block forever: when a fine item is dispensed, every coarse item has already
+// been dispensed to a running CTA, and coarse items never wait.  After
+// kMaxSpins polls the wait gives up, records WV_ERR_TIMEOUT and decodes
+// anyway (all reads stay in bounds).
+
+constexpr int kMaxSpins = 1 << 21;
+
+__device__ __forceinline__ int load_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_at_least(const int *flag, int target) {
+    for (int it = 0; it < kMaxSpins; ++it) {
+        if (load_acquire(flag) >= target) return true;
+        __nanosleep(256);
+    }
+    return false;
+}
+
+template <int WAV, int NB, bool FOV>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tiles_batch(const SurfaceJob *__restrict__ surfs, const uint2 *__restrict__ coarse,
+                  const uint2 *__restrict__ fine, int *cls, int *surf, int *err) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ TileArgs sa;
+    __shared__ uint2 s_item;
+    __shared__ int s_kind;   // 0 coarse, 1 fine, 2 no work left
+    float *A = smem;
+    const int nc = cls[1], nf = cls[2];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(&cls[0], 1);
+            if (item < nc) {
+                s_item = coarse[item];
+                s_kind = 0;
+            } else if (item < nc + nf) {
+                const uint2 w = fine[item - nc];
+                s_item = w;
+                s_kind = 1;
+                const int *c = surf + 2 * (int)w.x;
+                if (!wait_at_least(c + 1, c[0])) record_error(err, WV_ERR_TIMEOUT);
+            } else {
+                s_kind = 2;
+            }
+        }
+        __syncthreads();
+        const int kind = s_kind;
+        if (kind == 2) break;
+        const uint2 w = s_item;
+        const int *src = reinterpret_cast<const int *>(kind == 0 ? &surfs[w.x].coarse : &surfs[w.x].fine);
+        for (int k = threadIdx.x; k < (int)(sizeof(TileArgs) / 4); k += blockDim.x)
+            reinterpret_cast<int *>(&sa)[k] = __ldg(src + k);
+        __syncthreads();
+        float *P = smem + sa.a_floats;   // a_floats and p_floats fit the launch's shared memory
+        decode_one<WAV, NB, FOV>(sa, w.y, A, P);
+        if (kind == 0) __threadfence();   // LL_2 stores visible GPU-wide before the count
+        __syncthreads();
+        if (kind == 0 && threadIdx.x == 0) atomicAdd(&surf[2 * (int)w.x + 1], 1);
     }
 }
 
@@ -754,6 +824,8 @@ void smem_needs(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int 
 
 std::mutex g_cache_mutex;
 
+}  // namespace
+
 void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats) {
     static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> cache;
     std::lock_guard<std::mutex> lock(g_cache_mutex);
@@ -767,6 +839,23 @@ void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_float
     *a_floats = it->second.first;
     *p_floats = it->second.second;
 }
+
+// Shared-memory sizes and the folded 9/7 scales of a pass.
+void fill_tile_scales(TileArgs &a) {
+    smem_needs_cached(a.g.wavelet, a.l_top, a.l_bot, a.tile, &a.a_floats, &a.p_floats);
+    const double k2 = kK * kK;
+    for (int l = 0; l <= kMaxLevels; ++l) {
+        if (a.g.wavelet == WV_WAVELET_97) {
+            a.scale[l][0] = (float)(0.5 * a.g.step * pow(k2, a.g.levels));
+            a.scale[l][1] = a.scale[l][2] = (float)(0.5 * a.g.step * pow(k2, l - 1));
+            a.scale[l][3] = (float)(0.5 * a.g.step * pow(k2, l - 2));
+        } else {
+            a.scale[l][0] = a.scale[l][1] = a.scale[l][2] = a.scale[l][3] = 1.f;
+        }
+    }
+}
+
+namespace {
 
 template <int WAV, int NB>
 cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
@@ -784,18 +873,29 @@ cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
-    smem_needs_cached(a.g.wavelet, a.l_top, a.l_bot, a.tile, &a.a_floats, &a.p_floats);
-    const double k2 = kK * kK;
-    for (int l = 0; l <= kMaxLevels; ++l) {
-        if (a.g.wavelet == WV_WAVELET_97) {
-            a.scale[l][0] = (float)(0.5 * a.g.step * pow(k2, a.g.levels));
-            a.scale[l][1] = a.scale[l][2] = (float)(0.5 * a.g.step * pow(k2, l - 1));
-            a.scale[l][3] = (float)(0.5 * a.g.step * pow(k2, l - 2));
-        } else {
-            a.scale[l][0] = a.scale[l][1] = a.scale[l][2] = a.scale[l][3] = 1.f;
-        }
+template <int WAV, int NB, bool FOV>
+cudaError_t launch_batch_t(const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
+                           int *cls, int *surf, int *err, int smem_bytes, cudaStream_t cs) {
+    static int opted[64] = {};
+    int dev = 0, sms = 148, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || smem_bytes > opted[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_tiles_batch<WAV, NB, FOV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) opted[dev] = smem_bytes;
     }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_batch<WAV, NB, FOV>, kThreads,
+                                                                  smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    k_tiles_batch<WAV, NB, FOV><<<sms * per_sm, kThreads, smem_bytes, cs>>>(surfs, coarse, fine, cls, surf, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
+    fill_tile_scales(a);
     // the coarse pass has few, small tiles: 4-warp CTAs, four per SM (its
     // latency, not its work, sets its duration); tile passes: 8 warps, two
     const bool coarse = a.l_bot > 1;
@@ -835,7 +935,7 @@ TileArgs base_args(const Geom &g, const int16_t *payload, const int32_t *table, 
 
 int decode_tiles_smem_bytes(const Geom &g) {
     int af, pf;
-    smem_needs(g.wavelet, g.levels, 1, kTile, &af, &pf);
+    smem_needs(g.wavelet, g.levels, 1, g.tile, &af, &pf);
     return (af + pf) * 4;
 }
 
@@ -855,7 +955,7 @@ cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = g.levels;
     a.l_bot = 1;
-    a.tile = kTile;
+    a.tile = g.tile;
     for (int p = 0; p < 3; ++p) a.out_u8[p] = out_u8[p];
     a.out_f32 = out_f32;
     a.f32_plane = f32_plane;
@@ -872,7 +972,7 @@ cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const in
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = g.levels;
     a.l_bot = 3;
-    a.tile = kCoarseTile;
+    a.tile = g.ctile;
     for (int p = 0; p < 3; ++p) {
         a.ll_out[p] = ll2[p];
         a.ll_out_pitch[p] = ll2_pitch[p];
@@ -891,7 +991,7 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = 2;
     a.l_bot = 1;
-    a.tile = kTile;
+    a.tile = g.tile;
     for (int p = 0; p < 3; ++p) {
         a.ll_in[p] = ll2[p];
         a.ll_in_pitch[p] = ll2_pitch[p];
@@ -902,6 +1002,29 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
     a.tiles = tiles;
     a.count = count;
     return launch_args(a, cs);
+}
+
+// One persistent launch decoding every listed coarse and fine tile of a batch
+// (surfaces whose coefficient frames number nb).
+template <int WAV, bool FOV>
+cudaError_t launch_batch_nb(int nb, const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
+                            int *cls_ctr, int *surf_ctr, int *err, int smem_bytes, cudaStream_t cs) {
+    switch (nb) {
+    case 1: return launch_batch_t<WAV, 1, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 2: return launch_batch_t<WAV, 2, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 3: return launch_batch_t<WAV, 3, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    default: return launch_batch_t<WAV, 4, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    }
+}
+
+cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, const SurfaceJob *surfs,
+                                const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
+                                int *err, int smem_bytes, cudaStream_t cs) {
+    if (wavelet == WV_WAVELET_97)
+        return fovea ? launch_batch_nb<1, true>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
+                     : launch_batch_nb<1, false>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    return fovea ? launch_batch_nb<0, true>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
+                 : launch_batch_nb<0, false>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
 }
 
 }  // namespace wv

@@ -61,16 +61,6 @@ __device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {
                        (unsigned char)min(max(b, 0), 255), 255);
 }
 
-struct ResampleArgs {
-    View v;
-    const uint8_t *plane[3];
-    int w[3], h[3];
-    int planes, c420;
-    const float *uv;   // optional caller-given positions
-    uint8_t *out;
-    size_t pitch;
-};
-
 __device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, float v) {
     const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
     int cb = 128, cr = 128;
@@ -86,11 +76,10 @@ __device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, floa
     return to_rgba(y, cb, cr);
 }
 
-// Two horizontally adjacent pixels per thread (independent work for the
-// scheduler to overlap), written with one 8-byte store when aligned.
-__global__ void k_resample(ResampleArgs a) {
-    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+// Two horizontally adjacent pixels (i, j), (i + 1, j) per thread
+// (independent work for the scheduler to overlap), written with one 8-byte
+// store when aligned.
+__device__ __forceinline__ void resample_pair(const ResampleArgs &a, int i, int j) {
     if (i >= a.v.out_w || j >= a.v.out_h) return;
     const bool two = i + 1 < a.v.out_w;
     float u0, v0, u1 = 0.f, v1 = 0.f;
@@ -126,6 +115,16 @@ __global__ void k_resample(ResampleArgs a) {
     }
 }
 
+__global__ void k_resample(ResampleArgs a) {
+    resample_pair(a, 2 * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
+}
+
+// Batch: one z-slice of the grid per request.
+__global__ void k_resample_batch(const RequestJob *__restrict__ reqs) {
+    const ResampleArgs &a = reqs[blockIdx.z].rs;
+    resample_pair(a, 2 * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
+}
+
 }  // namespace
 
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
@@ -145,6 +144,12 @@ void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const 
     dim3 block(32, 8);
     dim3 grid((v.out_w + 63) / 64, (v.out_h + 7) / 8);
     k_resample<<<grid, block, 0, cs>>>(a);
+}
+
+void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs) {
+    dim3 block(32, 8);
+    dim3 grid((max_w + 63) / 64, (max_h + 7) / 8, n);
+    k_resample_batch<<<grid, block, 0, cs>>>(reqs);
 }
 
 }  // namespace wv

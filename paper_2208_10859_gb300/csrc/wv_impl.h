@@ -28,9 +28,9 @@ constexpr int kMaxLevels = 6;
 constexpr int kMaxBands = 4;    // 1 + tlevels, tlevels <= 3
 constexpr int kCell = 32;       // luma pixels per mask cell (256 cells at 8192)
 constexpr int kLogCell = 5;
-constexpr int kTile = 128;      // output tile side (plane pixels)
+constexpr int kTile = 128;      // default output tile side (plane pixels)
 constexpr int kThreads = 256;   // threads of the tile-decode CTA
-constexpr int kCoarseTile = 64; // coarse tile side at level 2 (256 plane pixels)
+constexpr int kCoarseTile = 64; // default coarse tile side at level 2 (256 plane pixels)
 
 // Subband index inside a level: 0 = LL (level L only), 1 = HL, 2 = LH, 3 = HH.
 struct PlaneGeom {
@@ -39,9 +39,10 @@ struct PlaneGeom {
     int nby[kMaxLevels + 1];
     int base[kMaxLevels + 1][4];       // first block id of (level, subband)
     int tiles_x, tiles_y;
-    int ctiles_x, ctiles_y;            // coarse tiles (kCoarseTile at level 2)
+    int ctiles_x, ctiles_y;            // coarse tiles (Geom::ctile samples of LL_2)
     int sub;                           // luma pixels per plane pixel (1 or 2)
     int ll2_pitch;                     // floats per row of the LL_2 plane
+    int tile_shift;                    // log2 of the mask cells per tile side
 };
 
 struct Geom {
@@ -51,6 +52,8 @@ struct Geom {
     int cells_x, cells_y;
     int total_tiles;
     int total_ctiles;
+    int tile;    // output tile side (plane pixels): 64 or 128
+    int ctile;   // coarse tile side (LL_2 samples): 32 or 64
 };
 
 // Coefficient frames that rebuild one frame (inverse inter-frame Haar):
@@ -78,6 +81,98 @@ struct Frustum {
     float n[4][3];
 };
 
+// Foveated decoding (Sec. 3.7): the details of level 1 are kept only in mask
+// cells whose centre lies within r1 of the gaze, those of level 2 within r2;
+// distance = max(|theta_x - gx|, |theta_y - gy|) in viewer angles (theta_x =
+// atan2(x, z), theta_y = atan2(y, z)), cells behind the viewer are outside.
+struct Fovea {
+    int on;
+    float gx, gy, r1, r2;
+};
+
+struct Range {
+    int lo, hi;
+};
+
+// Arguments of one tile-decode pass (levels l_top down to l_bot) over a list
+// of tiles of one decode target.
+struct TileArgs {
+    Geom g;
+    const int16_t *payload;
+    const int32_t *table;
+    Bands bands;
+    int l_top, l_bot;        // levels synthesised: l_top down to l_bot
+    int tile;                // output tile side at level l_bot - 1
+    const float *ll_in[3];   // LL_{l_top} planes when l_top < levels
+    int ll_in_pitch[3];
+    uint8_t *out_u8[3];      // l_bot == 1: samples
+    float *out_f32;          // l_bot == 1: float samples of plane f32_plane
+    int f32_plane;
+    float *ll_out[3];        // l_bot > 1: LL_{l_bot - 1} planes
+    int ll_out_pitch[3];
+    const uint8_t *fmask;    // foveation bits per mask cell (bit l-1: keep level l), or null
+    const uint32_t *tiles;   // tile list (count entries)
+    const int *count;
+    int *err;
+    int a_floats, p_floats;
+    // 9/7: half the dequantisation step times the synthesis band scaling
+    // folded over all levels.  Synthesis scales a low band by K and a high
+    // band by 1/K per axis at every level, the LL produced by level l + 1
+    // included; with LL_L x K^(2L), HL_l and LH_l x K^(2(l-1)), HH_l x
+    // K^(2(l-2)) the output of level l carries K^(2(l-1)), exactly the factor
+    // the next finer level expects of its LL, and level 1 returns unscaled
+    // samples.  (The half: the midpoint reconstruction is computed as
+    // (2q + sign q) step / 2.)
+    float scale[kMaxLevels + 1][4];
+};
+
+// Bilinear reprojection of one viewport from decoded planes.
+struct ResampleArgs {
+    View v;
+    const uint8_t *plane[3];
+    int w[3], h[3];
+    int planes, c420;
+    const float *uv;   // optional caller-given positions
+    uint8_t *out;
+    size_t pitch;
+};
+
+// ---- batched decoding ---------------------------------------------------------
+// A batch decodes many viewport requests of several streams.  Requests of the
+// same (stream, frame) without foveation share one decode target ("surface":
+// its own reconstruction and LL_2 planes); a foveated request has its own.
+struct SurfaceJob {
+    TileArgs coarse;   // levels L..3 into LL_2 (used when levels >= 3)
+    TileArgs fine;     // levels 2..1 from LL_2, or all levels when levels < 3
+    uint32_t *stamp;   // tile stamps (total_tiles), then coarse stamps (total_ctiles)
+    uint8_t *fmask;    // foveation cell bits (foveated surfaces), else null
+    int cls;           // decode class (see kClasses)
+};
+
+// Decode classes of a batch: one persistent tile-decode launch per wavelet,
+// foveation (a separately compiled kernel) and number of coefficient frames
+// present: class = 2 kMaxBands wavelet + kMaxBands foveated + frames - 1.
+constexpr int kClasses = 4 * kMaxBands;
+
+// Work lists of a batch, one pair per decode class.
+struct BatchLists {
+    uint2 *coarse[kClasses];
+    uint2 *fine[kClasses];
+};
+
+struct RequestJob {
+    View v;
+    Frustum f;
+    Fovea fov;
+    int surface;
+    ResampleArgs rs;
+};
+
+// Batch counters: decode class c uses [4c] next work item, [4c + 1] coarse
+// items, [4c + 2] fine items; surface s uses [kBatchCtr + 2s] coarse tiles
+// listed and [kBatchCtr + 2s + 1] coarse tiles finished.
+constexpr int kBatchCtr = 4 * kClasses;
+
 struct StreamHeader {
     char magic[4];
     uint32_t version, width, height, planes, c420, levels, wavelet, num_frames,
@@ -90,7 +185,7 @@ static_assert(sizeof(StreamHeader) == 88, "stream header layout");
 constexpr size_t kHeaderBytes = 128;
 
 // host helpers (api.cu)
-int build_geom(const wv_stream_desc &d, Geom *g);
+int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
 Bands frame_bands(const Geom &g, int frame);
 View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h);
 Frustum make_frustum(const View &v);
@@ -120,6 +215,18 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
                                const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs);
+void fill_tile_scales(TileArgs &a);
+void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats);
+
+// batched kernels
+void launch_footprint_batch(const RequestJob *reqs, const SurfaceJob *surfs, int n, int max_cx,
+                            int max_cy, cudaStream_t cs);
+void launch_select_batch(const SurfaceJob *surfs, int m, int max_stamps, const BatchLists &lists,
+                         int *ctr, cudaStream_t cs);
+cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, const SurfaceJob *surfs,
+                                const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
+                                int *err, int smem_bytes, cudaStream_t cs);
+void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 void launch_project(const View &v, float *uv, cudaStream_t cs);
 
 // encoder (encode.cu)
@@ -131,6 +238,7 @@ int encode_run(const Geom &g, const void *const *planes, void *scratch, size_t s
 
 struct wv_stream {
     wv::Geom g;
+    wv_stream_desc desc;
     int device = 0;
     cudaStream_t cs = nullptr;
     void *dmem = nullptr;

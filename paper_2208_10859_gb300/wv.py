@@ -45,7 +45,14 @@ class Image(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("s", ctypes.c_void_p), ("frame", ctypes.c_int), ("yaw", ctypes.c_float),
-                ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image)]
+                ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image),
+                ("fovea", ctypes.c_int), ("gaze_x", ctypes.c_float), ("gaze_y", ctypes.c_float),
+                ("r1", ctypes.c_float), ("r2", ctypes.c_float)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int), ("surfaces", ctypes.c_int), ("coarse_tiles", ctypes.c_int),
+                ("fine_tiles", ctypes.c_int), ("bytes", ctypes.c_size_t), ("ms", ctypes.c_double * 4)]
 
 
 class Profile(ctypes.Structure):
@@ -92,6 +99,19 @@ def _lib():
                                   ctypes.POINTER(c_size), vp]),
             "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
                                                c_int, vp]),
+            "wv_release_default_batch": (None, []),
+            "wv_batch_create": (c_int, [vp, ctypes.POINTER(vp)]),
+            "wv_batch_close": (None, [vp]),
+            "wv_batch_decode": (c_int, [vp, ctypes.POINTER(Request), c_int]),
+            "wv_batch_set_cuda_stream": (c_int, [vp, vp]),
+            "wv_batch_device_bytes": (c_int, [vp, ctypes.POINTER(Request), c_int, ctypes.POINTER(c_size)]),
+            "wv_batch_sync_status": (c_int, [vp]),
+            "wv_batch_stats": (c_int, [vp, ctypes.POINTER(BatchInfo)]),
+            "wv_batch_set_timing": (c_int, [vp, c_int]),
+            "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int]),
+            "wv_batch_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
+                                            ctypes.POINTER(c_int)]),
+            "wv_batch_autotune": (c_int, [vp, ctypes.POINTER(Request), c_int, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -109,7 +129,10 @@ def exported_symbols() -> list[str]:
             "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
             "wv_set_decode_mode",
-            "wv_encode_sizes", "wv_encode", "wv_decode_plane_static"]
+            "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
+            "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
+            "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
+            "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
 
 
 def _check(rc: int, what: str):
@@ -246,14 +269,87 @@ class ViewRequest:
     pitch: float
     fov: float
     out: object
+    fovea: bool = False
+    gaze_x: float = 0.0
+    gaze_y: float = 0.0
+    r1: float = float("inf")
+    r2: float = float("inf")
+
+
+def _requests(requests: list):
+    arr = (Request * len(requests))()
+    for i, r in enumerate(requests):
+        arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out),
+                         1 if r.fovea else 0, r.gaze_x, r.gaze_y, r.r1, r.r2)
+    return arr
 
 
 def decode_batch(requests: list, cuda_stream=None) -> None:
-    arr = (Request * len(requests))()
-    for i, r in enumerate(requests):
-        arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out))
+    arr = _requests(requests)
     _check(_lib().wv_decode_batch(arr, len(requests), ctypes.c_void_p(_cuda_stream_handle(cuda_stream))),
            "wv_decode_batch")
+
+
+class Batch:
+    """A batch context (wv_batch_*): batched, graph-launched decoding of many
+    viewport requests with an autotuned tile shape per stream class."""
+
+    def __init__(self, cuda_stream=None):
+        h = ctypes.c_void_p()
+        _check(_lib().wv_batch_create(ctypes.c_void_p(_cuda_stream_handle(cuda_stream)), ctypes.byref(h)),
+               "wv_batch_create")
+        self._h = h
+
+    def decode(self, requests: list) -> None:
+        arr = _requests(requests)
+        _check(_lib().wv_batch_decode(self._h, arr, len(requests)), "wv_batch_decode")
+
+    def set_cuda_stream(self, stream) -> None:
+        _check(_lib().wv_batch_set_cuda_stream(self._h, ctypes.c_void_p(_cuda_stream_handle(stream))),
+               "wv_batch_set_cuda_stream")
+
+    def device_bytes(self, requests: list) -> int:
+        n = ctypes.c_size_t()
+        _check(_lib().wv_batch_device_bytes(self._h, _requests(requests), len(requests), ctypes.byref(n)),
+               "wv_batch_device_bytes")
+        return n.value
+
+    def sync_status(self) -> int:
+        return _lib().wv_batch_sync_status(self._h)
+
+    def stats(self) -> dict:
+        info = BatchInfo()
+        _check(_lib().wv_batch_stats(self._h, ctypes.byref(info)), "wv_batch_stats")
+        return {"requests": info.requests, "surfaces": info.surfaces, "coarse_tiles": info.coarse_tiles,
+                "fine_tiles": info.fine_tiles, "bytes": info.bytes,
+                "ms": dict(zip(["footprint", "select", "decode", "resample"], list(info.ms)))}
+
+    def set_timing(self, on: bool) -> None:
+        _check(_lib().wv_batch_set_timing(self._h, 1 if on else 0), "wv_batch_set_timing")
+
+    def set_tile_shape(self, wavelet, levels, width, height, tile, ctile) -> None:
+        _check(_lib().wv_batch_set_tile_shape(self._h, wavelet, levels, width, height, tile, ctile),
+               "wv_batch_set_tile_shape")
+
+    def tile_shape(self, wavelet, levels, width, height) -> tuple:
+        t, c = ctypes.c_int(), ctypes.c_int()
+        _check(_lib().wv_batch_tile_shape(self._h, wavelet, levels, width, height, ctypes.byref(t),
+                                          ctypes.byref(c)), "wv_batch_tile_shape")
+        return t.value, c.value
+
+    def autotune(self, requests: list, reps: int = 3) -> None:
+        _check(_lib().wv_batch_autotune(self._h, _requests(requests), len(requests), reps), "wv_batch_autotune")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib().wv_batch_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def encode(frames, desc: dict, cuda_stream=None) -> bytes:

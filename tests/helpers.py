@@ -44,6 +44,19 @@ CASES["ragged97"] = (lambda: _ragged_frames(2, 25),
                      O.Params(320, 192, 3, 1, 4, O.WAVELET_97, 2, 1, 32, 2.0))
 
 
+# foveation workloads: 1024 x 512 YCbCr (32 x 16 mask cells), 4 levels
+CASES["fov97"] = (lambda: _wide_frames(2, 31),
+                  O.Params(1024, 512, 3, 1, 4, O.WAVELET_97, 2, 1, 64, 2.0))
+CASES["fov53"] = (lambda: _wide_frames(2, 33),
+                  O.Params(1024, 512, 3, 1, 3, O.WAVELET_53, 2, 1, 128, 2.0))
+
+
+def _wide_frames(n, seed):
+    """1024 x 512 YCbCr frames: the top half of a 1024 x 1024 equirect drawing."""
+    fr = synth.equirect_gop(1024, n, seed=seed, n_discs=8)
+    return [tuple(np.ascontiguousarray(p[: p.shape[0] // 2]) for p in f) for f in fr]
+
+
 @functools.lru_cache(maxsize=None)
 def case(name: str):
     """(frames, params, stream bytes, oracle Stream) of a named workload."""
