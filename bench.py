@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--poses", type=int, default=POSES, help=argparse.SUPPRESS)
     ap.add_argument("--out", type=int, default=OUT, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-decode leg")
     return ap.parse_args()
 
 
@@ -158,6 +159,126 @@ def traffic_record():
     if rec.get("ifwt_sha1") != hashlib.sha1(src).hexdigest():
         return None
     return rec
+
+
+# Batched workload: 12 streams of uneven size, wavelet and level count.
+BATCH_STREAMS = [(2048, 1, 4), (2048, 0, 4), (2048, 1, 5), (4096, 0, 5), (4096, 1, 5), (4096, 1, 6),
+                 (6144, 1, 4), (6144, 0, 5), (6144, 1, 6), (8192, 1, 5), (8192, 0, 6), (8192, 1, 6)]
+BATCH_REQUESTS = 256
+BATCH_WORKLOAD = ("256 foveated viewports per batch over 12 streams (2048^2, 4096^2, 6144^2, 8192^2 "
+                  "equirect YCbCr 4:2:0; 9/7 float32 and 5/3 integer; 4-6 levels; 8-frame groups, "
+                  "1-level inter-frame Haar, step 4, 256x256 blocks); FOV U[90, 120] deg, 2160x2160 RGBA; "
+                  "level-1 details within 20 deg of the gaze, level-2 within 40 deg")
+
+
+def batched_leg(args, dev, frames8k, stream):
+    """Config of many concurrent viewports: one batch (one CUDA graph, one
+    persistent tile-decode launch per decode class) against the plain
+    per-viewport decode of the same requests, same GPU, identical outputs."""
+    import torch
+    import synth
+    from paper_2208_10859_gb300 import wv
+    gops = {8192: frames8k}
+    for size in (2048, 4096, 6144):
+        gops[size] = synth.equirect_gop(size, FRAMES, seed=10 + size // 2048, n_discs=50)
+    streams = []
+    for size, wavelet, levels in BATCH_STREAMS:
+        d = dict(width=size, height=size, planes=3, chroma_420=1, levels=levels, wavelet=wavelet,
+                 num_frames=FRAMES, tlevels=TLEVELS, block=BLOCK, quant=0, step=STEP)
+        dfr = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in gops[size]]
+        streams.append(wv.Stream(wv.encode(dfr, d), cuda_stream=stream))
+        del dfr
+    del gops
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(7)
+    r1, r2 = math.radians(20), math.radians(40)
+    reqs = []
+    for k in range(BATCH_REQUESTS):
+        st = streams[int(rng.integers(len(streams)))]
+        out = torch.empty((args.out, args.out, 4), dtype=torch.uint8, device=dev)
+        reqs.append(wv.ViewRequest(st, int(rng.integers(FRAMES)), float(rng.uniform(-math.pi, math.pi)),
+                                   float(rng.uniform(-math.pi / 4, math.pi / 4)),
+                                   math.radians(float(rng.uniform(90, 120))), out, True,
+                                   float(rng.uniform(-0.15, 0.15)), float(rng.uniform(-0.15, 0.15)), r1, r2))
+    b = wv.Batch(stream)
+    b.autotune(reqs, reps=2)
+    shapes = {f"{sz}^2 {'9/7' if w else '5/3'} L{lv}": b.tile_shape(w, lv, sz, sz) for sz, w, lv in BATCH_STREAMS}
+    steps = max(3, args.steps // 2)
+    for _ in range(args.warmup):
+        b.decode(reqs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.decode(reqs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if b.sync_status() != 0:
+        raise RuntimeError("device error in the batched decode")
+    batch_ms = e0.elapsed_time(e1) / steps
+    info = b.stats()
+    batched_out = [r.out.clone() for r in reqs[:8]]
+    # per-step times (direct launches with events between the steps)
+    b.set_timing(True)
+    b.decode(reqs)
+    stage_ms = b.stats()["ms"]
+    b.set_timing(False)
+    # plain: the same requests one after the other, one request per launch
+    # sequence; completion time of each request within the burst
+    plain = wv.Batch(stream)
+    for r in reqs[:16]:
+        plain.decode([r])
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(reqs) + 1)]
+    evs[0].record(stream)
+    for i, r in enumerate(reqs):
+        plain.decode([r])
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    done = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
+    plain_ms = float(done[-1])
+    same = all(torch.equal(a, r.out) for a, r in zip(batched_out, reqs[:8]))
+    # unfoveated plain decode of the same poses (wv_decode_viewport)
+    for r in reqs[:16]:
+        r.stream.decode_viewport(r.frame, r.yaw, r.pitch, r.fov, r.out)
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    for r in reqs:
+        r.stream.decode_viewport(r.frame, r.yaw, r.pitch, r.fov, r.out)
+    u1.record(stream)
+    torch.cuda.synchronize()
+    unfov_ms = u0.elapsed_time(u1)
+    # algorithmic bytes on every 8th request (exact cone per request, host)
+    sample = reqs[::8]
+    alg = [sum(wv.request_bytes(r)) for r in sample]
+    alg_total = sum(alg) / len(sample) * len(reqs)
+    peak, _ = measured_peak_hbm()
+    dec_gbs = alg_total / (stage_ms["decode"] / 1e3) / 1e9
+    pct = lambda q: float(np.percentile(done, q))
+    plain.close()
+    b.close()
+    for st in streams:
+        st.close()
+    return {
+        "workload": BATCH_WORKLOAD,
+        "viewports_per_s": {"batched": BATCH_REQUESTS / (batch_ms / 1e3),
+                            "plain_per_viewport": BATCH_REQUESTS / (plain_ms / 1e3),
+                            "plain_unfoveated": BATCH_REQUESTS / (unfov_ms / 1e3)},
+        "burst_latency_ms": {"note": "all 256 requests arrive at t=0; a request's latency is its completion time",
+                             "batched_p50": batch_ms, "batched_p99": batch_ms,
+                             "plain_p50": pct(50), "plain_p99": pct(99)},
+        "batch_ms": batch_ms, "steps": steps, "stage_ms": stage_ms,
+        "surfaces": info["surfaces"], "coarse_tiles": info["coarse_tiles"], "fine_tiles": info["fine_tiles"],
+        "arena_bytes": info["bytes"], "tile_shapes": shapes,
+        "outputs_identical_batched_vs_plain": bool(same),
+        "decode_roofline": {"bound": "hbm", "achieved": dec_gbs, "peak": peak, "unit": "GB/s",
+                            "frac": dec_gbs / peak,
+                            "algorithmic_bytes": alg_total,
+                            "bytes_note": "coefficient cone (with foveation) + decoded region, exact on every 8th request, scaled to 256"},
+        "gpu_launches_per_batch": 3 + len({(r.stream.desc["wavelet"], r.stream.desc["tlevels"], r.fovea)
+                                           for r in reqs}),
+    }
 
 
 def cpu_baseline_leg(frames, poses, size, n_poses):
@@ -328,6 +449,10 @@ def run_ours(args):
     del keep
     e2e_value = e2e_steps * len(poses) * world / e2e_s
 
+    batched = None
+    if not args.no_batch:
+        batched = batched_leg(args, dev, frames, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_leg(frames, poses, size, args.cpu_poses)
@@ -362,6 +487,7 @@ def run_ours(args):
                                "rgba": out_bytes,
                                "whole_path_alg_GBps": (sum(cone) + len(poses) * out_bytes) * args.steps / (ms / 1e3) / 1e9},
             "clocks": clk.summary(),
+            "batched": batched,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

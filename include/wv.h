@@ -319,6 +319,21 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out);
  * filter supports, symmetric extension), restricted to stored blocks,
  * 2 bytes per coefficient, summed over the coefficient frames the
  * inter-frame rebuild reads.  Host computation. */
+/* As wv_cone_bytes with foveation: fovea_host (one byte per mask cell, host;
+ * bit 0 keeps the level-1 details of the cell, bit 1 the level-2 details;
+ * NULL keeps everything) drops the detail coefficients of levels 1 and 2
+ * whose nominal position (coefficient index x 2^level, in luma pixels) lies
+ * in a cell without the bit. */
+int wv_cone_bytes_fovea(wv_stream *s, int frame, const uint8_t *mask_host,
+                        const uint8_t *fovea_host, unsigned long long *bytes);
+
+/* Algorithmic bytes of one request: runs the request's footprint on the
+ * stream's CUDA stream (synchronising it), then on the host the coefficient
+ * bytes its cone reads (with the request's foveation, decided in double
+ * precision) and the bytes of the decoded region (marked cells x samples per
+ * cell over the planes). */
+int wv_request_bytes(const wv_request *r, unsigned long long *cone, unsigned long long *region);
+
 int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
                   unsigned long long *bytes);
 

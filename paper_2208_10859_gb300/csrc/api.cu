@@ -224,7 +224,10 @@ void dilate_axis(const std::vector<uint8_t> &in, std::vector<uint8_t> &out, int 
     }
 }
 
-unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask) {
+// fbits: optional foveation bits per mask cell (bit l - 1 keeps the details
+// of level l = 1, 2); dropped coefficients are not read.
+unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask,
+                              const uint8_t *fbits = nullptr) {
     const Geom &g = s->g;
     const Bands b = frame_bands(g, frame);
     unsigned long long total = 0;
@@ -237,6 +240,10 @@ unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask
             for (int x = 0; x < w; ++x)
                 R[(size_t)y * w + x] = mask[(size_t)(y / cell) * g.cells_x + x / cell] ? 1 : 0;
         auto count = [&](int level, int sub, int kx, int ky) {
+            if (fbits && level <= 2 && sub != 0) {
+                const int X = (kx << level) * pg.sub, Y = (ky << level) * pg.sub;
+                if (!((fbits[(size_t)(Y / kCell) * g.cells_x + X / kCell] >> (level - 1)) & 1)) return;
+            }
             const int bid = pg.base[level][sub] + (ky >> g.log2b) * pg.nbx[level] + (kx >> g.log2b);
             for (int k = 0; k < b.n; ++k)
                 if (s->table_host[(size_t)b.t[k] * g.nbpf + bid] >= 0) total += 2;
@@ -261,6 +268,28 @@ unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask
                 if (R[(size_t)y * w + x]) count(g.levels, 0, x, y);
     }
     return total;
+}
+
+// Foveation bits of every mask cell in double precision (the same definition
+// as the device footprint: cell centre direction, viewer angles, max norm).
+void fovea_bits_host(const Geom &g, double yaw, double pitch, const wv_request &r,
+                     std::vector<uint8_t> &out) {
+    const double pi = 3.14159265358979323846;
+    const double cy = cos(yaw), sy = sin(yaw), cp = cos(pitch), sp = sin(pitch);
+    const double R[9] = {cy, -sy * sp, sy * cp, 0.0, cp, sp, -sy, -cy * sp, cy * cp};
+    out.assign((size_t)g.cells_x * g.cells_y, 0);
+    for (int j = 0; j < g.cells_y; ++j)
+        for (int i = 0; i < g.cells_x; ++i) {
+            const double lon = 2.0 * pi * ((i + 0.5) * kCell / g.p[0].w - 0.5);
+            const double lat = pi * (0.5 - (j + 0.5) * kCell / g.p[0].h);
+            const double d[3] = {cos(lat) * sin(lon), sin(lat), cos(lat) * cos(lon)};
+            const double x = R[0] * d[0] + R[3] * d[1] + R[6] * d[2];
+            const double y = R[1] * d[0] + R[4] * d[1] + R[7] * d[2];
+            const double z = R[2] * d[0] + R[5] * d[1] + R[8] * d[2];
+            if (!(z > 0.0)) continue;
+            const double dist = std::max(fabs(atan2(x, z) - r.gaze_x), fabs(atan2(y, z) - r.gaze_y));
+            out[(size_t)j * g.cells_x + i] = (uint8_t)((dist <= r.r1 ? 1 : 0) | (dist <= r.r2 ? 2 : 0));
+        }
 }
 
 }  // namespace
@@ -582,6 +611,35 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
 int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host, unsigned long long *bytes) {
     if (!s || !mask_host || !bytes || frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
     *bytes = cone_bytes(s, frame, mask_host);
+    return WV_OK;
+}
+
+int wv_cone_bytes_fovea(wv_stream *s, int frame, const uint8_t *mask_host,
+                        const uint8_t *fovea_host, unsigned long long *bytes) {
+    if (!s || !mask_host || !bytes || frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
+    *bytes = cone_bytes(s, frame, mask_host, fovea_host);
+    return WV_OK;
+}
+
+int wv_request_bytes(const wv_request *r, unsigned long long *cone, unsigned long long *region) {
+    if (!r || !r->s || !cone || !region) return WV_ERR_ARG;
+    wv_stream *s = r->s;
+    const Geom &g = s->g;
+    if (r->frame < 0 || r->frame >= g.num_frames || r->out.width <= 0 || r->out.height <= 0)
+        return WV_ERR_ARG;
+    std::vector<uint8_t> mask((size_t)g.cells_x * g.cells_y);
+    int tiles = 0;
+    const int rc = wv_debug_footprint(s, r->yaw, r->pitch, r->fov, r->out.width, r->out.height,
+                                      mask.data(), &tiles);
+    if (rc != WV_OK) return rc;
+    std::vector<uint8_t> fb;
+    if (r->fovea) fovea_bits_host(g, r->yaw, r->pitch, *r, fb);
+    *cone = cone_bytes(s, r->frame, mask.data(), r->fovea ? fb.data() : nullptr);
+    unsigned long long cells = 0;
+    for (uint8_t m : mask) cells += m ? 1 : 0;
+    unsigned long long per_cell = 0;
+    for (int p = 0; p < g.planes; ++p) per_cell += (unsigned long long)(kCell / g.p[p].sub) * (kCell / g.p[p].sub);
+    *region = cells * per_cell;
     return WV_OK;
 }
 

@@ -100,6 +100,9 @@ def _lib():
             "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
                                                c_int, vp]),
             "wv_release_default_batch": (None, []),
+            "wv_cone_bytes_fovea": (c_int, [vp, c_int, vp, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+            "wv_request_bytes": (c_int, [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_ulonglong),
+                                         ctypes.POINTER(ctypes.c_ulonglong)]),
             "wv_batch_create": (c_int, [vp, ctypes.POINTER(vp)]),
             "wv_batch_close": (None, [vp]),
             "wv_batch_decode": (c_int, [vp, ctypes.POINTER(Request), c_int]),
@@ -130,6 +133,7 @@ def exported_symbols() -> list[str]:
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
             "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
+            "wv_cone_bytes_fovea", "wv_request_bytes",
             "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
             "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
@@ -226,11 +230,17 @@ class Stream:
         _check(_lib().wv_resample_at(self._handle, ctypes.c_void_p(uv.data_ptr()), ctypes.byref(img)),
                "wv_resample_at")
 
-    def cone_bytes(self, frame: int, mask: np.ndarray) -> int:
+    def cone_bytes(self, frame: int, mask: np.ndarray, fovea: np.ndarray | None = None) -> int:
         m = np.ascontiguousarray(mask, np.uint8)
         out = ctypes.c_ulonglong()
-        _check(_lib().wv_cone_bytes(self._handle, frame, m.ctypes.data_as(ctypes.c_void_p),
-                                    ctypes.byref(out)), "wv_cone_bytes")
+        if fovea is None:
+            _check(_lib().wv_cone_bytes(self._handle, frame, m.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(out)), "wv_cone_bytes")
+        else:
+            f = np.ascontiguousarray(fovea, np.uint8)
+            _check(_lib().wv_cone_bytes_fovea(self._handle, frame, m.ctypes.data_as(ctypes.c_void_p),
+                                              f.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)),
+                   "wv_cone_bytes_fovea")
         return out.value
 
     def set_decode_mode(self, mode: int) -> None:
@@ -282,6 +292,14 @@ def _requests(requests: list):
         arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out),
                          1 if r.fovea else 0, r.gaze_x, r.gaze_y, r.r1, r.r2)
     return arr
+
+
+def request_bytes(request) -> tuple:
+    """(coefficient cone bytes, decoded region bytes) of one request."""
+    arr = _requests([request])
+    cone, region = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    _check(_lib().wv_request_bytes(arr, ctypes.byref(cone), ctypes.byref(region)), "wv_request_bytes")
+    return cone.value, region.value
 
 
 def decode_batch(requests: list, cuda_stream=None) -> None:

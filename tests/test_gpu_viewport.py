@@ -163,6 +163,19 @@ def test_cone_bytes_match_oracle():
                 assert s.cone_bytes(frame, mask) == O.cone_bytes(st, frame, mask)
 
 
+def test_foveated_cone_bytes_match_oracle():
+    """Host accounting with foveation equals the oracle's cone restricted to
+    the kept coefficients, on seeded masks and the oracle's keep masks."""
+    _, p, _, st = H.case("fov97")
+    s = _stream("fov97")
+    for seed, (gx, gy, r1, r2) in [(1, (0.0, 0.0, 0.3, 0.6)), (2, (0.1, -0.05, 0.5, 0.9))]:
+        mask = synth.random_cell_mask(p.height // 32, p.width // 32, seed=seed, density=0.4)
+        keep = O.fovea_keep(p, 0.2, 0.1, gx, gy, r1, r2)
+        bits = keep[1].astype(np.uint8) | (keep[2].astype(np.uint8) << 1)
+        for frame in (0, 1):
+            assert s.cone_bytes(frame, mask, bits) == O.cone_bytes(st, frame, mask, keep)
+
+
 def test_batch_equals_single_and_bad_requests():
     from paper_2208_10859_gb300 import wv
     _, p, _, _ = H.case("yuv97")
