@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--out", type=int, default=OUT, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-decode leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     return ap.parse_args()
 
 
@@ -171,24 +172,33 @@ BATCH_WORKLOAD = ("256 foveated viewports per batch over 12 streams (2048^2, 409
                   "level-1 details within 20 deg of the gaze, level-2 within 40 deg")
 
 
+_GOPS = {}
+
+
+def gop(size, frames8k):
+    """Seeded synthetic 8-frame group of one size (the 8192 group is the main
+    workload's)."""
+    import synth
+    if size == SIZE:
+        return frames8k
+    if size not in _GOPS:
+        _GOPS[size] = synth.equirect_gop(size, FRAMES, seed=10 + size // 1024, n_discs=50)
+    return _GOPS[size]
+
+
 def batched_leg(args, dev, frames8k, stream):
     """Config of many concurrent viewports: one batch (one CUDA graph, one
     persistent tile-decode launch per decode class) against the plain
     per-viewport decode of the same requests, same GPU, identical outputs."""
     import torch
-    import synth
     from paper_2208_10859_gb300 import wv
-    gops = {8192: frames8k}
-    for size in (2048, 4096, 6144):
-        gops[size] = synth.equirect_gop(size, FRAMES, seed=10 + size // 2048, n_discs=50)
     streams = []
     for size, wavelet, levels in BATCH_STREAMS:
         d = dict(width=size, height=size, planes=3, chroma_420=1, levels=levels, wavelet=wavelet,
                  num_frames=FRAMES, tlevels=TLEVELS, block=BLOCK, quant=0, step=STEP)
-        dfr = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in gops[size]]
+        dfr = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in gop(size, frames8k)]
         streams.append(wv.Stream(wv.encode(dfr, d), cuda_stream=stream))
         del dfr
-    del gops
     torch.cuda.empty_cache()
     rng = np.random.default_rng(7)
     r1, r2 = math.radians(20), math.radians(40)
@@ -279,6 +289,88 @@ def batched_leg(args, dev, frames8k, stream):
         "gpu_launches_per_batch": 3 + len({(r.stream.desc["wavelet"], r.stream.desc["tlevels"], r.fovea)
                                            for r in reqs}),
     }
+
+
+# Serving workload: 8 streams of 4096^2-8192^2, 9/7, 5 levels; 32 headsets.
+SERVE_STREAMS = [(4096, 4.0), (4096, 6.0), (5120, 4.0), (6144, 4.0), (6144, 6.0), (7168, 4.0),
+                 (8192, 4.0), (8192, 6.0)]
+SERVE_HEADSETS, SERVE_HZ, SERVE_SIGMA_DEG, SERVE_SECONDS, SERVE_BUDGET_MS = 32, 90.0, 2.0, 2.0, 1000.0 / 90.0
+SERVE_WORKLOAD = ("32 simulated headsets, Poisson requests at 90 Hz each, random-walk yaw/pitch "
+                  "(sigma 2 deg per request), 110 deg FOV, 2160x2160 RGBA; 8 streams 4096^2-8192^2 "
+                  "(9/7, 5 levels, YCbCr 4:2:0, 8-frame groups, steps 4 and 6), video at 30 fps")
+
+
+def serving_leg(args, dev, frames8k, data8k):
+    """Request loop with continuous batching against the same loop without
+    batching (one request per launch, one slot), on the same arrival trace."""
+    import torch
+    from paper_2208_10859_gb300 import wv
+    blobs = []
+    for size, step in SERVE_STREAMS:
+        if size == SIZE and step == STEP:
+            blobs.append(data8k)
+            continue
+        d = dict(width=size, height=size, planes=3, chroma_420=1, levels=LEVELS, wavelet=1,
+                 num_frames=FRAMES, tlevels=TLEVELS, block=BLOCK, quant=0, step=step)
+        dfr = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in gop(size, frames8k)]
+        blobs.append(wv.encode(dfr, d))
+        del dfr
+    torch.cuda.empty_cache()
+    # arrival trace: per headset exponential gaps, random-walk poses
+    rng = np.random.default_rng(11)
+    events = []
+    for h in range(SERVE_HEADSETS):
+        t = float(rng.exponential(1.0 / SERVE_HZ))
+        yaw, pitch = float(rng.uniform(-math.pi, math.pi)), float(rng.uniform(-0.5, 0.5))
+        while t < SERVE_SECONDS + 0.3:
+            yaw += math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal())
+            pitch = float(np.clip(pitch + math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal()), -1.4, 1.4))
+            events.append((t, h, yaw, pitch, int(t * 30) % FRAMES))
+            t += float(rng.exponential(1.0 / SERVE_HZ))
+    events.sort()
+    ring = 6
+    bufs = [[torch.empty((OUT, OUT, 4), dtype=torch.uint8, device=dev) for _ in range(ring)]
+            for _ in range(SERVE_HEADSETS)]
+    fov = math.radians(FOV_DEG)
+
+    def run(slots, max_batch):
+        sv = wv.Server(slots=slots, max_batch=max_batch)
+        ids = [sv.add_stream(b) for b in blobs]
+        for i in range(len(ids)):          # warm: every stream resident, graphs captured
+            sv.wait(sv.submit(ids[i], 0, 0.0, 0.0, fov, bufs[0][0]))
+        last = [[None] * ring for _ in range(SERVE_HEADSETS)]
+        count = [0] * SERVE_HEADSETS
+        warm_end = 0.3
+        t0 = time.perf_counter()
+        reset = False
+        for (t, h, yaw, pitch, frame) in events:
+            while time.perf_counter() - t0 < t:
+                pass
+            if not reset and t >= warm_end:
+                sv.reset_stats()
+                reset = True
+            k = count[h] % ring
+            if last[h][k] is not None:
+                sv.wait(last[h][k])
+            last[h][k] = sv.submit(ids[h % len(ids)], frame, yaw, pitch, fov, bufs[h][k])
+            count[h] += 1
+        t_end = time.perf_counter() - t0
+        sv.drain()
+        elapsed = time.perf_counter() - t0 - warm_end
+        lat = sv.latencies()
+        st = sv.stats()
+        sv.close()
+        return {"viewports_per_s": len(lat) / elapsed, "requests": int(len(lat)),
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "max": float(lat.max())},
+                "within_budget": float(np.mean(lat <= SERVE_BUDGET_MS)),
+                "mean_batch": st["batched_requests"] / max(1, st["batches"]),
+                "slots": slots, "max_batch": max_batch, "offered_per_s": len(lat) / max(1e-9, t_end - warm_end)}
+
+    batching = run(3, 32)
+    plain = run(1, 1)
+    return {"workload": SERVE_WORKLOAD, "budget_ms": SERVE_BUDGET_MS,
+            "continuous_batching": batching, "plain_one_request_per_launch": plain}
 
 
 def cpu_baseline_leg(frames, poses, size, n_poses):
@@ -452,6 +544,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = batched_leg(args, dev, frames, stream)
+    serving = None
+    if not args.no_serve:
+        serving = serving_leg(args, dev, frames, data)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -488,6 +583,7 @@ def run_ours(args):
                                "whole_path_alg_GBps": (sum(cone) + len(poses) * out_bytes) * args.steps / (ms / 1e3) / 1e9},
             "clocks": clk.summary(),
             "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -253,6 +253,89 @@ int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int hei
                         int *ctile);
 int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching
+ * ------------------------------------------------------------------------- */
+
+typedef struct wv_server wv_server;
+
+typedef struct {
+    int slots;             /* batches in flight at once (one CUDA stream and
+                              batch context each), 1..16 */
+    int max_batch;         /* requests per batch, >= 1 */
+    size_t cache_bytes;    /* device bytes for resident streams; 0 = no limit */
+    size_t arena_bytes;    /* device bytes for the batch contexts of all
+                              slots; 0 = the free device memory minus
+                              reserve_bytes */
+    size_t reserve_bytes;  /* device memory left free when arena_bytes = 0 */
+} wv_server_config;
+
+/* One request of a client: as wv_request, with a stream registered by
+ * wv_server_add_stream instead of a wv_stream. */
+typedef struct {
+    int stream_id;
+    int frame;
+    float yaw, pitch, fov;
+    wv_image out;
+    int fovea;
+    float gaze_x, gaze_y;
+    float r1, r2;
+} wv_server_request;
+
+typedef struct {
+    unsigned long long submitted, completed, failed;
+    unsigned long long batches, batched_requests;   /* mean batch size = ratio */
+    unsigned long long uploads, evictions;          /* stream cache */
+    unsigned long long max_batch_bytes;             /* largest admitted batch */
+    unsigned long long resident_bytes;              /* streams on the device */
+    unsigned long long arena_bytes;                 /* batch contexts of all slots */
+} wv_server_stats;
+
+/* Start a server on the current device: `slots` CUDA streams with a batch
+ * context each and one worker thread.  Whenever a slot is free and requests
+ * are pending, the worker takes the oldest pending requests (at most
+ * max_batch), makes their streams resident (uploading from the registered
+ * host bytes, evicting the least recently used streams no batch in flight
+ * reads when cache_bytes would be exceeded), admits the longest prefix whose
+ * batch memory fits (arena_bytes, or the free device memory), and launches
+ * it as one batch (wv_batch_decode) on the slot's CUDA stream.  Requests
+ * arriving while batches run join the next batch; batches of different slots
+ * overlap on the GPU.  Each request's result equals the result of decoding
+ * it alone. */
+int wv_server_create(const wv_server_config *cfg, wv_server **out);
+
+/* Register a coded stream (bytes copied to pinned host memory; uploaded to
+ * the device when a batch first needs it).  *stream_id numbers the streams
+ * 0, 1, ... in registration order. */
+int wv_server_add_stream(wv_server *sv, const void *bytes, size_t n, int *stream_id);
+
+/* Queue a request (any thread).  The output image must stay valid until the
+ * request completes.  *ticket identifies it for wv_server_poll/wait. */
+int wv_server_submit(wv_server *sv, const wv_server_request *r, uint64_t *ticket);
+
+/* 1 while the request is pending or on the GPU; WV_OK once its output is
+ * written (the ticket is then released and *latency_ms, if not NULL, holds
+ * the time from submission to completion); a negative code if it failed. */
+int wv_server_poll(wv_server *sv, uint64_t ticket, double *latency_ms);
+
+/* As wv_server_poll, blocking up to timeout_ms (WV_ERR_TIMEOUT after). */
+int wv_server_wait(wv_server *sv, uint64_t ticket, double timeout_ms, double *latency_ms);
+
+/* Wait until no request is pending or in flight (WV_ERR_TIMEOUT after
+ * timeout_ms). */
+int wv_server_drain(wv_server *sv, double timeout_ms);
+
+int wv_server_get_stats(wv_server *sv, wv_server_stats *out);
+
+/* Latencies (ms, submission to completion) of the requests completed since
+ * the start or the last wv_server_reset_stats, in completion order: the
+ * first min(cap, *n) are copied to out; *n receives their number. */
+int wv_server_latencies(wv_server *sv, double *out, int cap, int *n);
+int wv_server_reset_stats(wv_server *sv);
+
+/* Stop the worker, wait for batches in flight, free everything. */
+void wv_server_close(wv_server *sv);
+
 /* Decode a whole plane of one frame (all tiles) -- the full-frame case, used
  * for the lossless workload and for parity checks.  dptr receives width x
  * height samples of the plane, row-major and tightly packed: uint8

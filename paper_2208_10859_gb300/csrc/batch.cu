@@ -411,6 +411,14 @@ int run_batch(wv_batch *b, const wv_request *reqs, int n, cudaStream_t cs) {
     return WV_OK;
 }
 
+}  // namespace
+
+namespace wv {
+size_t batch_held_bytes(const wv_batch *b) { return b ? b->dbytes : 0; }
+}  // namespace wv
+
+namespace {
+
 std::mutex g_default_mutex;
 std::map<int, wv_batch *> g_default;   // per device: the context of wv_decode_batch
 

@@ -227,6 +227,7 @@ cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, const SurfaceJo
                                 const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
                                 int *err, int smem_bytes, cudaStream_t cs);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
+size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);
 
 // encoder (encode.cu)

@@ -55,6 +55,24 @@ class BatchInfo(ctypes.Structure):
                 ("fine_tiles", ctypes.c_int), ("bytes", ctypes.c_size_t), ("ms", ctypes.c_double * 4)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_batch", ctypes.c_int), ("cache_bytes", ctypes.c_size_t),
+                ("arena_bytes", ctypes.c_size_t), ("reserve_bytes", ctypes.c_size_t)]
+
+
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int), ("frame", ctypes.c_int), ("yaw", ctypes.c_float),
+                ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image),
+                ("fovea", ctypes.c_int), ("gaze_x", ctypes.c_float), ("gaze_y", ctypes.c_float),
+                ("r1", ctypes.c_float), ("r2", ctypes.c_float)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_ulonglong) for n in
+                ("submitted", "completed", "failed", "batches", "batched_requests", "uploads", "evictions",
+                 "max_batch_bytes", "resident_bytes", "arena_bytes")]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int * 8), ("tiles", ctypes.c_int)]
 
@@ -100,6 +118,16 @@ def _lib():
             "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
                                                c_int, vp]),
             "wv_release_default_batch": (None, []),
+            "wv_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+            "wv_server_add_stream": (c_int, [vp, vp, c_size, ctypes.POINTER(c_int)]),
+            "wv_server_submit": (c_int, [vp, ctypes.POINTER(ServerRequest), ctypes.POINTER(ctypes.c_uint64)]),
+            "wv_server_poll": (c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+            "wv_server_wait": (c_int, [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+            "wv_server_drain": (c_int, [vp, ctypes.c_double]),
+            "wv_server_get_stats": (c_int, [vp, ctypes.POINTER(ServerStats)]),
+            "wv_server_latencies": (c_int, [vp, ctypes.POINTER(ctypes.c_double), c_int, ctypes.POINTER(c_int)]),
+            "wv_server_reset_stats": (c_int, [vp]),
+            "wv_server_close": (None, [vp]),
             "wv_cone_bytes_fovea": (c_int, [vp, c_int, vp, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
             "wv_request_bytes": (c_int, [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_ulonglong),
                                          ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -134,6 +162,9 @@ def exported_symbols() -> list[str]:
             "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
             "wv_cone_bytes_fovea", "wv_request_bytes",
+            "wv_server_create", "wv_server_add_stream", "wv_server_submit", "wv_server_poll",
+            "wv_server_wait", "wv_server_drain", "wv_server_get_stats", "wv_server_latencies",
+            "wv_server_reset_stats", "wv_server_close",
             "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
             "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
@@ -396,3 +427,74 @@ def encode(frames, desc: dict, cuda_stream=None) -> bytes:
                             ctypes.c_void_p(_cuda_stream_handle(cuda_stream))), "wv_encode")
     del mem, keep
     return out[:n.value].tobytes()
+
+
+class Server:
+    """Request loop with continuous batching (wv_server_*): register coded
+    streams, submit viewport requests from any thread, poll or wait."""
+
+    def __init__(self, slots: int = 2, max_batch: int = 64, cache_bytes: int = 0, arena_bytes: int = 0,
+                 reserve_bytes: int = 1 << 30):
+        h = ctypes.c_void_p()
+        cfg = ServerConfig(slots, max_batch, cache_bytes, arena_bytes, reserve_bytes)
+        _check(_lib().wv_server_create(ctypes.byref(cfg), ctypes.byref(h)), "wv_server_create")
+        self._h = h
+        self._keep = {}
+
+    def add_stream(self, data: bytes) -> int:
+        sid = ctypes.c_int()
+        _check(_lib().wv_server_add_stream(self._h, ctypes.c_char_p(data), len(data), ctypes.byref(sid)),
+               "wv_server_add_stream")
+        return sid.value
+
+    def submit(self, stream_id: int, frame: int, yaw: float, pitch: float, fov: float, out,
+               fovea: bool = False, gaze_x: float = 0.0, gaze_y: float = 0.0,
+               r1: float = float("inf"), r2: float = float("inf")) -> int:
+        r = ServerRequest(stream_id, frame, yaw, pitch, fov, _image(out), 1 if fovea else 0,
+                          gaze_x, gaze_y, r1, r2)
+        t = ctypes.c_uint64()
+        _check(_lib().wv_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "wv_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; the latency in ms once done (raises on failure)."""
+        lat = ctypes.c_double()
+        rc = _lib().wv_server_poll(self._h, ticket, ctypes.byref(lat))
+        if rc == 1:
+            return None
+        _check(rc, "wv_server_poll")
+        return lat.value
+
+    def wait(self, ticket: int, timeout_ms: float = 10000.0) -> float:
+        lat = ctypes.c_double()
+        _check(_lib().wv_server_wait(self._h, ticket, timeout_ms, ctypes.byref(lat)), "wv_server_wait")
+        return lat.value
+
+    def drain(self, timeout_ms: float = 60000.0) -> None:
+        _check(_lib().wv_server_drain(self._h, timeout_ms), "wv_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib().wv_server_get_stats(self._h, ctypes.byref(st)), "wv_server_get_stats")
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def latencies(self) -> np.ndarray:
+        n = ctypes.c_int()
+        _check(_lib().wv_server_latencies(self._h, None, 0, ctypes.byref(n)), "wv_server_latencies")
+        buf = (ctypes.c_double * max(1, n.value))()
+        _check(_lib().wv_server_latencies(self._h, buf, n.value, ctypes.byref(n)), "wv_server_latencies")
+        return np.array(buf[:n.value])
+
+    def reset_stats(self) -> None:
+        _check(_lib().wv_server_reset_stats(self._h), "wv_server_reset_stats")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib().wv_server_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
