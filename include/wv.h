@@ -336,6 +336,59 @@ int wv_server_reset_stats(wv_server *sv);
 /* Stop the worker, wait for batches in flight, free everything. */
 void wv_server_close(wv_server *sv);
 
+/* ---------------------------------------------------------------------------
+ * Learned post-filter (an extension; the paper has no learned component)
+ * ------------------------------------------------------------------------- */
+
+/* A residual CNN on the decoded viewport's luma that removes quantisation
+ * artefacts.  Input x = Y / 255 (float, n images of h x w, row-major); five
+ * 3x3 convolutions with zero padding: 1 -> 32 channels (ReLU), three
+ * 32 -> 32 (ReLU), 32 -> 1; output y = x + that residual.  Parameters are a
+ * flat float array, layer by layer: weights [c_out][c_in][3][3] (row dy,
+ * column dx; cross-correlation), then biases [c_out]; wv_cnn_param_count()
+ * floats in all.  Weights run as bf16 with fp32 accumulation on the tensor
+ * cores (tcgen05); activations between layers are bf16.  Training (MSE loss,
+ * Adam on fp32 master parameters) runs on the same kernels.  Calls are
+ * enqueued on cuda_stream (NULL = legacy default stream); a network object
+ * is used by one host thread at a time. */
+typedef struct wv_cnn wv_cnn;
+
+size_t wv_cnn_param_count(void);
+
+/* Create a network with the given parameters (host, wv_cnn_param_count()
+ * floats) on the current device. */
+int wv_cnn_create(const float *params_host, wv_cnn **out);
+void wv_cnn_close(wv_cnn *c);
+int wv_cnn_get_params(wv_cnn *c, float *params_host);
+/* Replace the parameters (and reset the optimiser state). */
+int wv_cnn_set_params(wv_cnn *c, const float *params_host);
+
+/* y = network(x) for n images of h x w (device float planes). */
+int wv_cnn_forward(wv_cnn *c, const float *x_dev, float *y_dev, int n, int h, int w, void *cuda_stream);
+
+/* Loss mean((y - t)^2) and its gradient with respect to every parameter
+ * (host, wv_cnn_param_count() floats, same layout as the parameters);
+ * synchronises cuda_stream. */
+int wv_cnn_gradients(wv_cnn *c, const float *x_dev, const float *t_dev, int n, int h, int w,
+                     float *grads_host, float *loss_host, void *cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * batch (x, t).  loss_host != NULL receives the batch loss before the step
+ * (synchronises cuda_stream). */
+int wv_cnn_train_step(wv_cnn *c, const float *x_dev, const float *t_dev, int n, int h, int w, float lr,
+                      float *loss_host, void *cuda_stream);
+
+/* Synchronise the device and read the network's error word (WV_ERR_TIMEOUT:
+ * a bounded tensor-core wait gave up). */
+int wv_cnn_sync_status(wv_cnn *c);
+
+/* wv_decode_viewport with the post-filter: the decoded region is reprojected
+ * into the viewport's luma and chroma, the network filters the luma, and the
+ * last layer's epilogue converts to RGBA (8-bit luma: floor(255 y + 1/2),
+ * clamped).  Enqueued on the stream's CUDA stream. */
+int wv_decode_viewport_filtered(wv_stream *s, int frame, float yaw, float pitch, float fov, wv_cnn *c,
+                                const wv_image *out);
+
 /* Decode a whole plane of one frame (all tiles) -- the full-frame case, used
  * for the lossless workload and for parity checks.  dptr receives width x
  * height samples of the plane, row-major and tightly packed: uint8

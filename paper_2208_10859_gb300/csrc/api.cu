@@ -168,6 +168,31 @@ cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, flo
     return e;
 }
 
+}  // namespace
+
+namespace wv {
+
+// Steps 1-3 of a viewport decode: footprint, tile lists and the tile decode
+// of the region an out_w x out_h viewport reads (into the stream's
+// reconstruction planes).
+int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h) {
+    const Geom &g = s->g;
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
+    const Bands b = frame_bands(g, frame);
+    const uint32_t gen = next_gen(s);
+    prof_begin(s, kKFootprint);
+    launch_footprint(g, v, s->mask, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
+    prof_end(s);
+    prof_begin(s, kKTiles);
+    launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
+    prof_end(s);
+    return run_decode(s, b, s->recon, nullptr, -1) == cudaSuccess ? WV_OK : WV_ERR_CUDA;
+}
+
+}  // namespace wv
+
+namespace {
+
 int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
                     const wv_image *out) {
     if (!s) return WV_ERR_ARG;
@@ -175,18 +200,9 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     if (!(fov > 0.f && fov < 3.14159f) || !isfinite(yaw) || !isfinite(pitch)) return WV_ERR_ARG;
     if (check_image(out) != WV_OK) return WV_ERR_ARG;
     const Geom &g = s->g;
+    const int rc = wv::decode_region(s, frame, yaw, pitch, fov, out->width, out->height);
+    if (rc != WV_OK) return rc;
     const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, g.p[0].h);
-    const Bands b = frame_bands(g, frame);
-    uint8_t *m = s->mask;
-    const uint32_t gen = next_gen(s);
-    prof_begin(s, kKFootprint);
-    launch_footprint(g, v, m, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
-    prof_end(s);
-    prof_begin(s, kKTiles);
-    launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
-    prof_end(s);
-    cudaError_t e = run_decode(s, b, s->recon, nullptr, -1);
-    if (e != cudaSuccess) return WV_ERR_CUDA;
     prof_begin(s, kKResample);
     launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
     prof_end(s);

@@ -11,18 +11,13 @@
 // coefficients rounded to 1/65536, result rounded half up and clamped.
 // The paper itself stores no colour transform (Sec. 5); the YCbCr 4:2:0
 // stream and this conversion belong to this decoder's format.
+#include <string.h>
+
 #include "wv_impl.h"
 
 namespace wv {
 
 namespace {
-
-// BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb.
-constexpr double kKr = 0.2126, kKb = 0.0722, kKg = 1.0 - kKr - kKb;
-constexpr int kRCr = (int)(2.0 * (1.0 - kKr) * 65536.0 + 0.5);
-constexpr int kGCb = (int)(2.0 * kKb * (1.0 - kKb) / kKg * 65536.0 + 0.5);
-constexpr int kGCr = (int)(2.0 * kKr * (1.0 - kKr) / kKg * 65536.0 + 0.5);
-constexpr int kBCb = (int)(2.0 * (1.0 - kKb) * 65536.0 + 0.5);
 
 // Bilinear sample of an 8-bit plane (w x h, row-major) at (u, v): x wraps
 // (projected positions lie in [-1/2, w - 1/2), so one conditional add
@@ -50,17 +45,6 @@ __device__ __forceinline__ int bilinear_u8(const uint8_t *__restrict__ img, int 
     return ((256 - fy) * top + fy * bot + 32768) >> 16;
 }
 
-__device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {
-    const int yy = y * 65536 + 32768;
-    cb -= 128;
-    cr -= 128;
-    const int r = (yy + kRCr * cr) >> 16;
-    const int g = (yy - kGCb * cb - kGCr * cr) >> 16;
-    const int b = (yy + kBCb * cb) >> 16;
-    return make_uchar4((unsigned char)min(max(r, 0), 255), (unsigned char)min(max(g, 0), 255),
-                       (unsigned char)min(max(b, 0), 255), 255);
-}
-
 __device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, float v) {
     const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
     int cb = 128, cr = 128;
@@ -79,8 +63,34 @@ __device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, floa
 // Two horizontally adjacent pixels (i, j), (i + 1, j) per thread
 // (independent work for the scheduler to overlap), written with one 8-byte
 // store when aligned.
+// Luma / 255, Cb and Cr of viewport pixel (i, j) into the planes.
+__device__ __forceinline__ void sample_ycc(const ResampleArgs &a, int i, int j) {
+    float u, v;
+    project_px(a.v, i, j, u, v);
+    const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
+    int cb = 128, cr = 128;
+    if (a.planes == 3) {
+        float uc = u, vc = v;
+        if (a.c420) {
+            uc = fmaf(u + 0.5f, 0.5f, -0.5f);
+            vc = fmaf(v + 0.5f, 0.5f, -0.5f);
+        }
+        cb = bilinear_u8(a.plane[1], a.w[1], a.h[1], uc, vc);
+        cr = bilinear_u8(a.plane[2], a.w[2], a.h[2], uc, vc);
+    }
+    const size_t o = (size_t)j * a.v.out_w + i;
+    a.y_plane[o] = (float)y * (1.0f / 255.0f);
+    a.cb_plane[o] = (uint8_t)cb;
+    a.cr_plane[o] = (uint8_t)cr;
+}
+
 __device__ __forceinline__ void resample_pair(const ResampleArgs &a, int i, int j) {
     if (i >= a.v.out_w || j >= a.v.out_h) return;
+    if (a.y_plane) {
+        sample_ycc(a, i, j);
+        if (i + 1 < a.v.out_w) sample_ycc(a, i + 1, j);
+        return;
+    }
     const bool two = i + 1 < a.v.out_w;
     float u0, v0, u1 = 0.f, v1 = 0.f;
     if (a.uv) {
@@ -128,8 +138,13 @@ __global__ void k_resample_batch(const RequestJob *__restrict__ reqs) {
 }  // namespace
 
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
-                     uint8_t *out, size_t pitch, cudaStream_t cs) {
+                     uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane,
+                     uint8_t *cb_plane, uint8_t *cr_plane) {
     ResampleArgs a;
+    memset(&a, 0, sizeof(a));
+    a.y_plane = y_plane;
+    a.cb_plane = cb_plane;
+    a.cr_plane = cr_plane;
     a.v = v;
     for (int p = 0; p < 3; ++p) {
         a.plane[p] = recon[p];

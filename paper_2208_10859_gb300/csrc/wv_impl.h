@@ -135,6 +135,10 @@ struct ResampleArgs {
     const float *uv;   // optional caller-given positions
     uint8_t *out;
     size_t pitch;
+    // instead of RGBA: luma / 255 (float) and 8-bit Cb, Cr planes of the
+    // viewport (out_w x out_h, tightly packed), for the post-filter
+    float *y_plane;
+    uint8_t *cb_plane, *cr_plane;
 };
 
 // ---- batched decoding ---------------------------------------------------------
@@ -185,6 +189,7 @@ static_assert(sizeof(StreamHeader) == 88, "stream header layout");
 constexpr size_t kHeaderBytes = 128;
 
 // host helpers (api.cu)
+int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h);
 int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
 Bands frame_bands(const Geom &g, int frame);
 View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h);
@@ -214,7 +219,8 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
                                uint8_t *const *out_u8, float *out_f32, int f32_plane,
                                const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
-                     uint8_t *out, size_t pitch, cudaStream_t cs);
+                     uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane = nullptr,
+                     uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr);
 void fill_tile_scales(TileArgs &a);
 void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats);
 
@@ -306,6 +312,26 @@ __device__ __forceinline__ void fixed_split(float t, int &i, int &f) {
     i = (int)fl;
     f = (int)floorf(fmaf(t - fl, 256.0f, 0.5f));
     if (f >= 256) { f = 0; i += 1; }
+}
+
+// BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb.
+constexpr double kKr = 0.2126, kKb = 0.0722, kKg = 1.0 - kKr - kKb;
+constexpr int kRCr = (int)(2.0 * (1.0 - kKr) * 65536.0 + 0.5);
+constexpr int kGCb = (int)(2.0 * kKb * (1.0 - kKb) / kKg * 65536.0 + 0.5);
+constexpr int kGCr = (int)(2.0 * kKr * (1.0 - kKr) / kKg * 65536.0 + 0.5);
+constexpr int kBCb = (int)(2.0 * (1.0 - kKb) * 65536.0 + 0.5);
+
+// YCbCr (8-bit, full range) -> RGBA8 with the integer BT.709 coefficients,
+// rounded half up and clamped.
+__device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {
+    const int yy = y * 65536 + 32768;
+    cb -= 128;
+    cr -= 128;
+    const int r = (yy + kRCr * cr) >> 16;
+    const int g = (yy - kGCb * cb - kGCr * cr) >> 16;
+    const int b = (yy + kBCb * cb) >> 16;
+    return make_uchar4((unsigned char)min(max(r, 0), 255), (unsigned char)min(max(g, 0), 255),
+                       (unsigned char)min(max(b, 0), 255), 255);
 }
 
 __device__ __forceinline__ void record_error(int *err, int code) {

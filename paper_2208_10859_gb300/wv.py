@@ -118,6 +118,16 @@ def _lib():
             "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
                                                c_int, vp]),
             "wv_release_default_batch": (None, []),
+            "wv_cnn_param_count": (c_size, []),
+            "wv_cnn_create": (c_int, [vp, ctypes.POINTER(vp)]),
+            "wv_cnn_close": (None, [vp]),
+            "wv_cnn_get_params": (c_int, [vp, vp]),
+            "wv_cnn_set_params": (c_int, [vp, vp]),
+            "wv_cnn_forward": (c_int, [vp, vp, vp, c_int, c_int, c_int, vp]),
+            "wv_cnn_gradients": (c_int, [vp, vp, vp, c_int, c_int, c_int, vp, ctypes.POINTER(fl), vp]),
+            "wv_cnn_train_step": (c_int, [vp, vp, vp, c_int, c_int, c_int, fl, ctypes.POINTER(fl), vp]),
+            "wv_cnn_sync_status": (c_int, [vp]),
+            "wv_decode_viewport_filtered": (c_int, [vp, c_int, fl, fl, fl, vp, ctypes.POINTER(Image)]),
             "wv_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
             "wv_server_add_stream": (c_int, [vp, vp, c_size, ctypes.POINTER(c_int)]),
             "wv_server_submit": (c_int, [vp, ctypes.POINTER(ServerRequest), ctypes.POINTER(ctypes.c_uint64)]),
@@ -162,6 +172,9 @@ def exported_symbols() -> list[str]:
             "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
             "wv_cone_bytes_fovea", "wv_request_bytes",
+            "wv_cnn_param_count", "wv_cnn_create", "wv_cnn_close", "wv_cnn_get_params", "wv_cnn_set_params",
+            "wv_cnn_forward", "wv_cnn_gradients", "wv_cnn_train_step", "wv_cnn_sync_status",
+            "wv_decode_viewport_filtered",
             "wv_server_create", "wv_server_add_stream", "wv_server_submit", "wv_server_poll",
             "wv_server_wait", "wv_server_drain", "wv_server_get_stats", "wv_server_latencies",
             "wv_server_reset_stats", "wv_server_close",
@@ -273,6 +286,11 @@ class Stream:
                                               f.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)),
                    "wv_cone_bytes_fovea")
         return out.value
+
+    def decode_viewport_filtered(self, frame: int, yaw: float, pitch: float, fov: float, cnn, out) -> None:
+        img = _image(out)
+        _check(_lib().wv_decode_viewport_filtered(self._handle, frame, yaw, pitch, fov, cnn.handle,
+                                                  ctypes.byref(img)), "wv_decode_viewport_filtered")
 
     def set_decode_mode(self, mode: int) -> None:
         _check(_lib().wv_set_decode_mode(self._handle, mode), "wv_set_decode_mode")
@@ -492,6 +510,97 @@ class Server:
         if getattr(self, "_h", None) and self._h.value:
             _lib().wv_server_close(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# learned post-filter
+# ---------------------------------------------------------------------------
+
+CNN_SHAPES = [(32, 1), (32, 32), (32, 32), (32, 32), (1, 32)]   # (c_out, c_in) per layer
+
+
+def cnn_init_params(seed: int = 0) -> np.ndarray:
+    """Flat parameters: He-normal weights (the last layer scaled by 0.1, so the
+    untrained network is close to the identity), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (co, ci) in enumerate(CNN_SHAPES):
+        std = np.sqrt(2.0 / (9 * ci)) * (0.1 if k == len(CNN_SHAPES) - 1 else 1.0)
+        parts.append((rng.standard_normal((co, ci, 3, 3)) * std).ravel())
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _fptr(t) -> ctypes.c_void_p:
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class CNN:
+    """The residual post-filter network (wv_cnn_*): forward, gradients and
+    Adam training steps on the library's tensor-core kernels."""
+
+    def __init__(self, params=None, seed: int = 0):
+        p = cnn_init_params(seed) if params is None else np.ascontiguousarray(params, np.float32)
+        if p.size != self.param_count():
+            raise ValueError("wrong parameter count")
+        h = ctypes.c_void_p()
+        _check(_lib().wv_cnn_create(p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "wv_cnn_create")
+        self.handle = h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(_lib().wv_cnn_param_count())
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.param_count(), np.float32)
+        _check(_lib().wv_cnn_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "wv_cnn_get_params")
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, np.float32)
+        _check(_lib().wv_cnn_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)), "wv_cnn_set_params")
+
+    def forward(self, x, stream=None):
+        import torch
+        n, h, w = x.shape
+        y = torch.empty_like(x)
+        _check(_lib().wv_cnn_forward(self.handle, _fptr(x), _fptr(y), n, h, w,
+                                     ctypes.c_void_p(_cuda_stream_handle(stream))), "wv_cnn_forward")
+        return y
+
+    def gradients(self, x, t, stream=None):
+        n, h, w = x.shape
+        g = np.empty(self.param_count(), np.float32)
+        loss = ctypes.c_float()
+        _check(_lib().wv_cnn_gradients(self.handle, _fptr(x), _fptr(t), n, h, w, g.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(loss), ctypes.c_void_p(_cuda_stream_handle(stream))),
+               "wv_cnn_gradients")
+        return float(loss.value), g
+
+    def train_step(self, x, t, lr: float, want_loss: bool = False, stream=None):
+        n, h, w = x.shape
+        loss = ctypes.c_float()
+        _check(_lib().wv_cnn_train_step(self.handle, _fptr(x), _fptr(t), n, h, w, lr,
+                                        ctypes.byref(loss) if want_loss else None,
+                                        ctypes.c_void_p(_cuda_stream_handle(stream))), "wv_cnn_train_step")
+        return float(loss.value) if want_loss else None
+
+    def sync_status(self) -> int:
+        return _lib().wv_cnn_sync_status(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib().wv_cnn_close(self.handle)
+            self.handle = ctypes.c_void_p()
 
     def __del__(self):
         try:

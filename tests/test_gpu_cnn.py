@@ -1,0 +1,154 @@
+"""GPU tests of the learned post-filter (wv_cnn_*): the tensor-core forward
+pass and every parameter gradient against the fp64 CPU oracle; training on
+(decoded, original) pairs from the oracle codec improves PSNR over the
+unfiltered decode on held-out frames; the filtered viewport decode with a
+zero residual equals the plain viewport decode."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import cnn as OC
+import synth
+import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def to_layers(flat):
+    """Flat parameters -> oracle list of (w, b)."""
+    out, o = [], 0
+    for co, ci in OC.SHAPES:
+        nw = co * ci * 9
+        w = flat[o:o + nw].astype(np.float64).reshape(co, ci, 3, 3)
+        o += nw
+        b = flat[o:o + co].astype(np.float64)
+        o += co
+        out.append((w, b))
+    assert o == flat.size
+    return out
+
+
+def bf16_round(a):
+    """Round to bfloat16 (nearest even) and back, in numpy."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _net(seed, last_scale=8.0):
+    from paper_2208_10859_gb300 import wv
+    p = wv.cnn_init_params(seed)
+    n_last = 32 * 9 + 1
+    p[-n_last:] *= last_scale           # a residual of visible size
+    p[-1] = 0.01
+    return wv.CNN(p), p
+
+
+def test_param_layout_matches_oracle():
+    from paper_2208_10859_gb300 import wv
+    assert wv.CNN.param_count() == sum(co * ci * 9 + co for co, ci in OC.SHAPES)
+
+
+@pytest.mark.parametrize("shape", [(2, 37, 150), (1, 8, 128), (3, 9, 5)])
+def test_forward_matches_oracle(shape):
+    """y = x + r: the residual within 3 % of its largest magnitude of the fp64
+    oracle run on the network's bf16-rounded weights (activations are bf16
+    between layers on the GPU), and its relative L2 error below 1 %."""
+    net, p = _net(1)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 1, shape)
+    y = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    layers = [(bf16_round(w), b) for w, b in to_layers(p)]
+    yo, _ = OC.forward(layers, x)
+    r_gpu, r_or = y - x, yo - x
+    scale = np.abs(r_or).max()
+    assert scale > 1e-2
+    assert np.abs(r_gpu - r_or).max() <= 0.03 * scale, np.abs(r_gpu - r_or).max() / scale
+    assert np.linalg.norm(r_gpu - r_or) <= 0.01 * np.linalg.norm(r_or)
+    assert net.sync_status() == 0
+
+
+def test_gradients_match_oracle():
+    """Every layer's weight and bias gradient, and the loss, against the fp64
+    oracle's chain rule: relative L2 error below 3 %, cosine above 0.999."""
+    net, p = _net(3)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, (2, 21, 140))
+    t = np.clip(x + 0.05 * rng.standard_normal(x.shape), 0, 1)
+    loss, g = net.gradients(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                            torch.tensor(t, dtype=torch.float32, device="cuda"))
+    layers = [(bf16_round(w), b) for w, b in to_layers(p)]
+    lo, go = OC.backward(layers, x, t)
+    assert loss == pytest.approx(lo, rel=1e-2)
+    gl = to_layers(g)
+    for k, ((dw, db), (dwo, dbo)) in enumerate(zip(gl, go)):
+        for a, b in ((dw.ravel(), dwo.ravel()), (db, dbo)):
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert rel < 3e-2 and cos > 0.999, (k, rel, cos)
+    assert net.sync_status() == 0
+
+
+def _pairs(n_frames, seed, step):
+    """(decoded, original) luma pairs from the oracle codec: 256^2 grey frames,
+    4-level CDF 9/7, dead-zone step `step`."""
+    frames = synth.equirect_gop(256, n_frames, seed=seed, n_discs=12, chroma=False)
+    p = O.Params(256, 256, 1, 0, 4, O.WAVELET_97, n_frames, 0, 64, float(step))
+    st = O.Stream(O.encode(frames, p))
+    dec = np.stack([O.decode_plane(st, f, 0)[1] for f in range(n_frames)])
+    org = np.stack([f[0] for f in frames])
+    return dec.astype(np.float32) / 255, org.astype(np.float32) / 255
+
+
+def test_training_gains_psnr_over_plain_decode():
+    from paper_2208_10859_gb300 import wv
+    dtr, otr = _pairs(8, seed=41, step=16)
+    dte, ote = _pairs(2, seed=42, step=16)
+    net = wv.CNN(seed=5)
+    xs = torch.tensor(dtr, device="cuda")
+    ts = torch.tensor(otr, device="cuda")
+    rng = np.random.default_rng(6)
+    losses = []
+    for it in range(400):
+        idx = rng.integers(0, 8, 16)
+        ys, xs0 = rng.integers(0, 256 - 64, 16), rng.integers(0, 256 - 64, 16)
+        xb = torch.stack([xs[i, a:a + 64, b:b + 64] for i, a, b in zip(idx, ys, xs0)]).contiguous()
+        tb = torch.stack([ts[i, a:a + 64, b:b + 64] for i, a, b in zip(idx, ys, xs0)]).contiguous()
+        lr = 2e-3 if it < 300 else 5e-4
+        losses.append(net.train_step(xb, tb, lr, want_loss=(it % 50 == 0)))
+    assert net.sync_status() == 0
+    y = net.forward(torch.tensor(dte, device="cuda")).cpu().numpy()
+    y8 = np.clip(np.floor(y * 255 + 0.5), 0, 255)
+    before = OC.psnr(dte * 255, ote * 255)
+    after = OC.psnr(y8, ote * 255)
+    print(f"held-out PSNR: decode {before:.2f} dB, filtered {after:.2f} dB; losses {[l for l in losses if l]}")
+    assert after > before + 0.2
+
+
+def test_filtered_viewport_with_zero_residual_is_the_plain_viewport():
+    from paper_2208_10859_gb300 import wv
+    _, p, data, _ = H.case("yuv97")
+    s = wv.Stream(data)
+    flat = wv.cnn_init_params(7)
+    flat[-(32 * 9 + 1):] = 0.0           # last layer zero: y = x
+    net = wv.CNN(flat)
+    for yaw, pitch in [(0.3, 0.2), (-2.0, -0.7)]:
+        a = torch.zeros((70, 90, 4), dtype=torch.uint8, device="cuda")
+        b = torch.zeros_like(a)
+        s.decode_viewport(1, yaw, pitch, math.radians(100), a)
+        s.decode_viewport_filtered(1, yaw, pitch, math.radians(100), net, b)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    # a trained-looking residual changes the picture, within a bounded amount
+    net2, _ = _net(8)
+    c = torch.zeros((70, 90, 4), dtype=torch.uint8, device="cuda")
+    s.decode_viewport_filtered(1, 0.3, 0.2, math.radians(100), net2, c)
+    s.decode_viewport(1, 0.3, 0.2, math.radians(100), a)
+    torch.cuda.synchronize()
+    d = np.abs(c.cpu().numpy().astype(int) - a.cpu().numpy().astype(int))
+    assert d.max() > 0 and np.all(c.cpu().numpy()[..., 3] == 255)
+    assert s.sync_status() == 0 and net.sync_status() == 0
