@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-decode leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-filter", action="store_true", help="skip the post-filter leg")
     return ap.parse_args()
 
 
@@ -373,6 +374,97 @@ def serving_leg(args, dev, frames8k, data8k):
             "continuous_batching": batching, "plain_one_request_per_launch": plain}
 
 
+FILTER_STEPS = (4.0, 12.0)
+
+
+def postfilter_leg(args, dev, frames8k, s, poses, stream):
+    """Decode + learned post-filter on 2160x2160 viewports of the 8192^2
+    workload (step 4, and the same frames coded at step 12), against the
+    plain decode, in PSNR to the viewport of the original frames and in
+    viewports/s; the network's forward pass alone against the bf16 peak."""
+    import torch
+    from paper_2208_10859_gb300 import wv
+    from paper_2208_10859_gb300.train_postfilter import nearest_weights
+    fov = math.radians(FOV_DEG)
+    dfr = [tuple(torch.from_numpy(pl).to(dev) for pl in f) for f in frames8k]
+    lossless = wv.Stream(wv.encode(dfr, dict(width=SIZE, height=SIZE, planes=3, chroma_420=1, levels=3, wavelet=0,
+                                              num_frames=FRAMES, tlevels=0, block=BLOCK, quant=0, step=1.0)),
+                         cuda_stream=stream)
+    streams = {STEP: s}
+    for q in FILTER_STEPS:
+        if q != STEP:
+            d = desc(SIZE)
+            d["step"] = q
+            streams[q] = wv.Stream(wv.encode(dfr, d), cuda_stream=stream)
+    del dfr
+    torch.cuda.empty_cache()
+    sel = poses[:8]
+    res = {}
+    ref = [torch.empty((OUT, OUT, 4), dtype=torch.uint8, device=dev) for _ in sel]
+    for i, (yaw, pitch) in enumerate(sel):
+        lossless.decode_viewport(i % FRAMES, yaw, pitch, fov, ref[i])
+
+    def psnr(a, b):
+        d = (a[..., :3].float() - b[..., :3].float())
+        return float(10 * torch.log10(255.0 ** 2 / (d * d).mean()))
+
+    flops = 2.0 * OUT * OUT * sum(9 * ci * co for co, ci in wv.CNN_SHAPES)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for q in FILTER_STEPS:
+        st = streams[q]
+        net = wv.CNN(np.fromfile(nearest_weights(q), "<f4"))
+        plain = [torch.empty((OUT, OUT, 4), dtype=torch.uint8, device=dev) for _ in sel]
+        filt = [torch.empty((OUT, OUT, 4), dtype=torch.uint8, device=dev) for _ in sel]
+        for i, (yaw, pitch) in enumerate(sel):
+            st.decode_viewport(i % FRAMES, yaw, pitch, fov, plain[i])
+            st.decode_viewport_filtered(i % FRAMES, yaw, pitch, fov, net, filt[i])
+        torch.cuda.synchronize()
+        p_plain = float(np.mean([psnr(a, r) for a, r in zip(plain, ref)]))
+        p_filt = float(np.mean([psnr(a, r) for a, r in zip(filt, ref)]))
+        times = {}
+        for name, fn in (("plain", st.decode_viewport), ("filtered", None)):
+            e0.record(stream)
+            for rep in range(3):
+                for i, (yaw, pitch) in enumerate(sel):
+                    if fn is None:
+                        st.decode_viewport_filtered(i % FRAMES, yaw, pitch, fov, net, filt[i])
+                    else:
+                        fn(i % FRAMES, yaw, pitch, fov, plain[i])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / (3 * len(sel))
+        x = torch.rand((1, OUT, OUT), device=dev)
+        net.forward(x, stream=stream)
+        e0.record(stream)
+        for _ in range(5):
+            net.forward(x, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cnn_ms = e0.elapsed_time(e1) / 5
+        if net.sync_status() != 0:
+            raise RuntimeError("device error in the post-filter")
+        res[f"step {q:g}"] = {"psnr_plain_db": p_plain, "psnr_filtered_db": p_filt, "gain_db": p_filt - p_plain,
+                               "ms_per_viewport": times, "viewports_per_s_filtered": 1e3 / times["filtered"],
+                               "network_ms": cnn_ms, "network_tflops": flops / (cnn_ms / 1e3) / 1e12,
+                               "weights": os.path.basename(nearest_weights(q))}
+        net.close()
+    for q, st in streams.items():
+        if st is not s:
+            st.close()
+    lossless.close()
+    peak = 1938.8
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return {"workload": "2160x2160 viewports (8 poses) of the 8192^2 workload at steps 4 and 12; PSNR over RGB "
+                        "against the same viewports of the original frames (5/3 lossless stream)",
+            "network": "5 x conv3x3 (1-32-32-32-32-1), ReLU, luma residual; bf16 weights and activations, fp32 "
+                       "accumulation (tcgen05)",
+            "flops_per_viewport": flops, "bf16_peak_tflops": peak, "results": res}
+
+
 def cpu_baseline_leg(frames, poses, size, n_poses):
     """Time the oracle as it stands (single-threaded plain decoder: whole
     frame, then reprojection) on n_poses viewports.  The oracle decodes a
@@ -547,6 +639,9 @@ def run_ours(args):
     serving = None
     if not args.no_serve:
         serving = serving_leg(args, dev, frames, data)
+    postfilter = None
+    if not args.no_filter:
+        postfilter = postfilter_leg(args, dev, frames, s, poses, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -584,6 +679,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "batched": batched,
             "serving": serving,
+            "postfilter": postfilter,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -1,0 +1,130 @@
+"""Train the residual post-filter (wv_cnn_*) on the GPU and write its
+parameters.
+
+Training pairs: seeded synthetic equirectangular luma frames (band-limited
+noise and textured discs, 2048 x 2048), coded with the library's encoder
+(5-level CDF 9/7 at one dead-zone step: 4, 6, 8, 12 or 16) and decoded with
+the library's decoder (which matches the CPU reference codec within 1e-4 of
+the 8-bit scale); 256 x 256 crops of (decoded, original) luma / 255.  One
+parameter set per step (the artefacts differ in strength; a single set
+smooths low-distortion frames too much).  The network is trained with the
+library's own forward/backward kernels (MSE, Adam).  A held-out set of
+frames gives the PSNR before and after.
+
+    python -m paper_2208_10859_gb300.train_postfilter --step 4
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+STEPS = (4.0, 6.0, 8.0, 12.0, 16.0)
+
+
+def weights_path(step: float) -> str:
+    """Parameter file of the network trained for quantiser step `step`."""
+    return os.path.join(HERE, "weights", f"postfilter_q{int(step)}.bin")
+
+
+def nearest_weights(step: float) -> str:
+    return weights_path(min(STEPS, key=lambda s: abs(s - step)))
+
+
+SIZE, PATCH = 2048, 256
+
+
+def coded_pairs(wv, torch, seeds, steps, frames_per_seed=8):
+    """Decoded and original luma (float32 / 255, on the device) per frame and step."""
+    sys.path.insert(0, ROOT)
+    import synth
+    dec, org = [], []
+    for seed in seeds:
+        fr = synth.equirect_gop(SIZE, frames_per_seed, seed=seed, n_discs=30, chroma=False)
+        dev = [tuple(torch.from_numpy(p).cuda() for p in f) for f in fr]
+        for step in steps:
+            desc = dict(width=SIZE, height=SIZE, planes=1, chroma_420=0, levels=5, wavelet=1,
+                        num_frames=frames_per_seed, tlevels=0, block=256, quant=0, step=step)
+            s = wv.Stream(wv.encode(dev, desc))
+            for f in range(frames_per_seed):
+                out = torch.empty((SIZE, SIZE), dtype=torch.uint8, device="cuda")
+                s.decode_full(f, 0, out)
+                dec.append(out.float() / 255)
+                org.append(dev[f][0].float() / 255)
+            torch.cuda.synchronize()
+            s.close()
+        del dev
+    return torch.stack(dec), torch.stack(org)
+
+
+def psnr(a, b) -> float:
+    mse = float(((a - b) ** 2).mean())
+    return 10 * math.log10(1.0 / mse)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--step", type=float, required=True, choices=STEPS)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--patches", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--epochs", type=float, default=2.0)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    import torch
+    sys.path.insert(0, ROOT)
+    from paper_2208_10859_gb300 import wv
+    import __graft_entry__
+    __graft_entry__.build()
+    t0 = time.time()
+    out = args.out or weights_path(args.step)
+    dec, org = coded_pairs(wv, torch, (101, 102, 103, 104, 105, 106), (args.step,))
+    tdec, torg = coded_pairs(wv, torch, (201,), (args.step,), frames_per_seed=4)
+    g = torch.Generator(device="cpu").manual_seed(args.seed)
+    nfr = dec.shape[0]
+    idx = torch.randint(0, nfr, (args.patches,), generator=g)
+    ys = torch.randint(0, SIZE - PATCH + 1, (args.patches,), generator=g)
+    xs = torch.randint(0, SIZE - PATCH + 1, (args.patches,), generator=g)
+    net = wv.CNN(seed=args.seed)
+    steps = int(args.epochs * args.patches / args.batch)
+    log = []
+    t1 = time.time()
+    for it in range(steps):
+        sel = torch.randint(0, args.patches, (args.batch,), generator=g)
+        xb = torch.stack([dec[idx[k], ys[k]:ys[k] + PATCH, xs[k]:xs[k] + PATCH] for k in sel.tolist()])
+        tb = torch.stack([org[idx[k], ys[k]:ys[k] + PATCH, xs[k]:xs[k] + PATCH] for k in sel.tolist()])
+        lr = args.lr * (0.5 * (1 + math.cos(math.pi * it / steps)) * 0.9 + 0.1)
+        loss = net.train_step(xb.contiguous(), tb.contiguous(), lr, want_loss=(it % 200 == 0))
+        if loss is not None:
+            log.append((it, loss))
+            print(f"step {it}/{steps} loss {loss:.3e}", flush=True)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    if net.sync_status() != 0:
+        raise RuntimeError("device error during training")
+    # held-out PSNR
+    x = tdec.contiguous()
+    y = net.forward(x)
+    y8 = torch.clamp(torch.floor(y * 255 + 0.5), 0, 255) / 255
+    res = {"step": args.step, "decode_psnr": psnr(x, torg), "filtered_psnr": psnr(y8, torg)}
+    p = net.params()
+    os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
+    p.astype("<f4").tofile(out)
+    meta = {"patches": args.patches, "patch": PATCH, "batch": args.batch, "steps": steps, "lr": args.lr,
+            "train_seconds": train_s, "total_seconds": time.time() - t0, "loss_log": log,
+            "held_out_psnr": res, "params": int(p.size)}
+    with open(os.path.splitext(out)[0] + ".json", "w") as f:
+        json.dump(meta, f, indent=1)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
