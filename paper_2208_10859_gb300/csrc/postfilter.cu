@@ -46,7 +46,7 @@ constexpr int kTilePx = 128;            // pixels per MMA tile (M)
 constexpr int kRowPx = kTilePx + 2;     // input pixels of one row slot (1-pixel halo)
 constexpr int kLbo = kRowPx * 16;       // bytes between the 8-channel columns of a slot
 constexpr int kSlot = 4 * kLbo;         // one input row: 4 columns of 8 channels
-constexpr int kStrip = 8;               // output rows per CTA
+constexpr int kStrip = 16;              // output rows per work item
 constexpr int kStep32 = 32 * 32;        // bytes of one K-step of a 32-row operand
 constexpr int kBMid = 18 * kStep32;     // 32 x 288
 constexpr int kBLast = 18 * 16 * 32;    // 16 x 288 (row 0 real)
@@ -96,16 +96,21 @@ __device__ __forceinline__ size_t pix(const ConvArgs &a, int img, int y, int x) 
 
 // Epilogue of the 32-channel modes for one pixel: bias + ReLU, or the ReLU
 // gate of the layer below; bf16 NHWC store.
-__device__ __forceinline__ void store32(const ConvArgs &a, size_t p, const float (&v)[32]) {
+__device__ __forceinline__ void load_gate(const ConvArgs &a, size_t p, uint4 (&g)[4]) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.gate + p * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q] = __ldg(src + q);
+}
+
+__device__ __forceinline__ void store32(const ConvArgs &a, size_t p, const float (&v)[32], const uint4 (&gate)[4]) {
     float o[32];
     if (a.mode == kRelu) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) o[c] = fmaxf(v[c] + (a.bias ? __ldg(a.bias + c) : 0.f), 0.f);
     } else {
-        const uint4 *g = reinterpret_cast<const uint4 *>(a.gate + p * kC);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint4 gv = __ldg(g + q);
+            const uint4 gv = gate[q];
             const bf16 *gb = reinterpret_cast<const bf16 *>(&gv);
 #pragma unroll
             for (int e = 0; e < 8; ++e) o[8 * q + e] = __bfloat162float(gb[e]) > 0.f ? v[8 * q + e] : 0.f;
@@ -158,7 +163,6 @@ __global__ void __launch_bounds__(128) k_conv_mid(ConvArgs a, int nb) {
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kStrip, img = blockIdx.z;
     const int bbytes = nb == 32 ? kBMid : kBLast;
     for (int i = tid * 16; i < bbytes; i += 128 * 16)
         *reinterpret_cast<uint4 *>(sB + i) = __ldg(reinterpret_cast<const uint4 *>(a.wpack + i));
@@ -171,54 +175,85 @@ __global__ void __launch_bounds__(128) k_conv_mid(ConvArgs a, int nb) {
     const uint32_t idesc = nb == 32 ? umma::idesc_bf16(128, 32) : umma::idesc_bf16(128, 16);
     const int bstep = nb * 32;
     uint32_t phase = 0;
-    const int y1 = min(y0 + kStrip, a.h);
-    for (int y = y0; y < y1; ++y) {
-        for (int r = (y == y0 ? y - 1 : y + 1); r <= y + 1; ++r) {   // rows not yet in a slot
-            uint8_t *slot = slots + ((r + 3) % 3) * kSlot;
-            const bool rin = r >= 0 && r < a.h;
-            for (int idx = tid; idx < kRowPx * 4; idx += 128) {
-                const int px = idx >> 2, c = idx & 3, gx = x0 - 1 + px;
-                uint4 val = make_uint4(0u, 0u, 0u, 0u);
-                if (rin && gx >= 0 && gx < a.w)
-                    val = __ldg(reinterpret_cast<const uint4 *>(a.in + pix(a, img, r, gx) * kC + c * 8));
-                *reinterpret_cast<uint4 *>(slot + c * kLbo + px * 16) = val;
-            }
-        }
-        umma::fence_smem_to_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-        if (tid == 0) {
-            const uint32_t sb = umma::smem_addr(sB);
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;
-                const uint32_t abase = umma::smem_addr(slots + ((y + dy - 1 + 3) % 3) * kSlot) + dx * 16;
+    // input row r: 130 pixels x 4 columns of 8 channels, 16 bytes each,
+    // staged through registers so that the next row's loads overlap the
+    // MMAs and the epilogue of the current one
+    constexpr int kPer = (kRowPx * 4 + 127) / 128;
+    uint4 pre[kPer];
+    auto load_row = [&](int img, int x0, int r) {
+        const bool rin = r >= 0 && r < a.h;
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
-                    umma::mma(tmem, umma::desc(abase + 2 * s * kLbo, kLbo, 128),
-                              umma::desc(sb + (tap * 2 + s) * bstep, 128, 256), idesc, tap > 0 || s > 0);
-            }
-            umma::commit(&mbar);
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = tid + 128 * j;
+            const int px = idx >> 2, c = idx & 3, gx = x0 - 1 + px;
+            pre[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (idx < kRowPx * 4 && rin && gx >= 0 && gx < a.w)
+                pre[j] = __ldg(reinterpret_cast<const uint4 *>(a.in + pix(a, img, r, gx) * kC + c * 8));
         }
-        const bool got = __syncthreads_and(umma::mbar_wait(&mbar, phase));
-        phase ^= 1;
-        if (!got) {
-            if (tid == 0) record_error(a.err, WV_ERR_TIMEOUT);
-            break;
+    };
+    auto store_row = [&](int r) {
+        uint8_t *slot = slots + ((r + 3) % 3) * kSlot;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = tid + 128 * j;
+            if (idx < kRowPx * 4) *reinterpret_cast<uint4 *>(slot + (idx & 3) * kLbo + (idx >> 2) * 16) = pre[j];
         }
-        umma::fence_after_sync();
-        float v[32];
-        umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    };
+    // work items: strips of kStrip rows x 128 pixels, CTA b takes b, b + grid, ...
+    const int tiles_x = (a.w + kTilePx - 1) / kTilePx, strips = (a.h + kStrip - 1) / kStrip;
+    const int items = tiles_x * strips * a.n;
+    bool ok = true;
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int img = it / (tiles_x * strips), sy = (it / tiles_x) % strips;
+        const int x0 = (it % tiles_x) * kTilePx, y0 = sy * kStrip, y1 = min(y0 + kStrip, a.h);
+        // the slots are free: the previous item's MMAs have completed
+        for (int r = y0 - 1; r <= y0 + 1; ++r) {
+            load_row(img, x0, r);
+            store_row(r);
+        }
         const int xg = x0 + tid;
         const bool valid = xg < a.w;
-        if (nb == 32) {
-            if (valid) store32(a, pix(a, img, y, xg), v);
-        } else {
-            store_last(a, valid ? pix(a, img, y, xg) : 0, v[0], valid);
+        for (int y = y0; y < y1; ++y) {
+            umma::fence_smem_to_async();
+            umma::fence_before_sync();
+            __syncthreads();
+            umma::fence_after_sync();
+            if (tid == 0) {
+                const uint32_t sb = umma::smem_addr(sB);
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t abase = umma::smem_addr(slots + ((y + dy - 1 + 3) % 3) * kSlot) + dx * 16;
+#pragma unroll
+                    for (int s = 0; s < 2; ++s)
+                        umma::mma(tmem, umma::desc(abase + 2 * s * kLbo, kLbo, 128),
+                                  umma::desc(sb + (tap * 2 + s) * bstep, 128, 256), idesc, tap > 0 || s > 0);
+                }
+                umma::commit(&mbar);
+            }
+            const bool more = y + 1 < y1;
+            if (more) load_row(img, x0, y + 2);
+            uint4 gate[4] = {};
+            if (nb == 32 && a.mode == kGate && valid) load_gate(a, pix(a, img, y, xg), gate);
+            const bool got = __syncthreads_and(umma::mbar_wait(&mbar, phase));
+            phase ^= 1;
+            if (!got) {
+                if (tid == 0) record_error(a.err, WV_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            umma::fence_after_sync();
+            float v[32];
+            umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+            if (nb == 32) {
+                if (valid) store32(a, pix(a, img, y, xg), v, gate);
+            } else {
+                store_last(a, valid ? pix(a, img, y, xg) : 0, v[0], valid);
+            }
+            // the slot of row y - 1 is free: this row's MMAs have completed
+            if (more) store_row(y + 2);
+            umma::fence_before_sync();
         }
-        umma::fence_before_sync();
-        __syncthreads();
     }
     __syncthreads();
     if (warp == 0) umma::tmem_free<32>(tmem);
@@ -278,7 +313,9 @@ __global__ void __launch_bounds__(128) k_conv_in1(ConvArgs a) {
         umma::fence_after_sync();
         float v[32];
         umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-        if (xg < a.w) store32(a, pix(a, img, y, xg), v);
+        uint4 gate[4] = {};
+        if (a.mode == kGate && xg < a.w) load_gate(a, pix(a, img, y, xg), gate);
+        if (xg < a.w) store32(a, pix(a, img, y, xg), v, gate);
         umma::fence_before_sync();
         __syncthreads();
     }
@@ -612,8 +649,9 @@ cudaError_t launch_mid(const ConvArgs &a, int nb, cudaStream_t cs) {
         if (e != cudaSuccess) return e;
         opted[dev] = 1;
     }
-    dim3 grid((a.w + kTilePx - 1) / kTilePx, (a.h + kStrip - 1) / kStrip, a.n);
-    k_conv_mid<<<grid, 128, smem, cs>>>(a, nb);
+    // one work item (strip) per CTA: measured faster than persistent CTAs
+    const int items = ((a.w + kTilePx - 1) / kTilePx) * ((a.h + kStrip - 1) / kStrip) * a.n;
+    k_conv_mid<<<items, 128, smem, cs>>>(a, nb);
     return cudaGetLastError();
 }
 
