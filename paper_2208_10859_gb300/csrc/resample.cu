@@ -19,11 +19,16 @@ namespace wv {
 
 namespace {
 
-// Bilinear sample of an 8-bit plane (w x h, row-major) at (u, v): x wraps
+// The 2 x 2 taps of a bilinear sample of a w x h plane at (u, v): x wraps
 // (projected positions lie in [-1/2, w - 1/2), so one conditional add
-// suffices; other positions take a modulo), y clamps.
-__device__ __forceinline__ int bilinear_u8(const uint8_t *__restrict__ img, int w, int h,
-                                           float u, float v) {
+// suffices; other positions take a modulo), y clamps.  Offsets into the
+// row-major plane (planes are < 2^31 bytes) and 1/256 weights.
+struct Taps {
+    int a0, a1, b0, b1;   // (ya, xa), (ya, xb), (yb, xa), (yb, xb)
+    int fx, fy;
+};
+
+__device__ __forceinline__ Taps bilinear_taps(int w, int h, float u, float v) {
     int x0, fx, y0, fy;
     fixed_split(u, x0, fx);
     fixed_split(v, y0, fy);
@@ -35,55 +40,64 @@ __device__ __forceinline__ int bilinear_u8(const uint8_t *__restrict__ img, int 
         if (xa < 0) xa += w;
     }
     const int xb = (xa + 1 == w) ? 0 : xa + 1;
-    const int ya = min(max(y0, 0), h - 1);
-    const int yb = min(max(y0 + 1, 0), h - 1);
-    const uint8_t *ra = img + ya * w, *rb = img + yb * w;   // planes are < 2^31 bytes
-    const int p00 = __ldg(ra + xa), p01 = __ldg(ra + xb);
-    const int p10 = __ldg(rb + xa), p11 = __ldg(rb + xb);
-    const int wx1 = fx, wx0 = 256 - fx;
-    const int top = wx0 * p00 + wx1 * p01, bot = wx0 * p10 + wx1 * p11;
-    return ((256 - fy) * top + fy * bot + 32768) >> 16;
+    const int ya = min(max(y0, 0), h - 1) * w;
+    const int yb = min(max(y0 + 1, 0), h - 1) * w;
+    Taps t;
+    t.a0 = ya + xa;
+    t.a1 = ya + xb;
+    t.b0 = yb + xa;
+    t.b1 = yb + xb;
+    t.fx = fx;
+    t.fy = fy;
+    return t;
 }
 
-__device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, float v) {
-    const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
-    int cb = 128, cr = 128;
+__device__ __forceinline__ int blend(const uint8_t *__restrict__ img, const Taps &t) {
+    const int p00 = __ldg(img + t.a0), p01 = __ldg(img + t.a1);
+    const int p10 = __ldg(img + t.b0), p11 = __ldg(img + t.b1);
+    const int wx1 = t.fx, wx0 = 256 - t.fx;
+    const int top = wx0 * p00 + wx1 * p01, bot = wx0 * p10 + wx1 * p11;
+    return ((256 - t.fy) * top + t.fy * bot + 32768) >> 16;
+}
+
+// Y, Cb, Cr of luma position (u, v); Cb and Cr share their taps.
+__device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, float v, int &y, int &cb,
+                                             int &cr) {
+    y = blend(a.plane[0], bilinear_taps(a.w[0], a.h[0], u, v));
+    cb = cr = 128;
     if (a.planes == 3) {
         float uc = u, vc = v;
         if (a.c420) {
             uc = fmaf(u + 0.5f, 0.5f, -0.5f);
             vc = fmaf(v + 0.5f, 0.5f, -0.5f);
         }
-        cb = bilinear_u8(a.plane[1], a.w[1], a.h[1], uc, vc);
-        cr = bilinear_u8(a.plane[2], a.w[2], a.h[2], uc, vc);
+        const Taps t = bilinear_taps(a.w[1], a.h[1], uc, vc);
+        cb = blend(a.plane[1], t);
+        cr = blend(a.plane[2], t);
     }
+}
+
+__device__ __forceinline__ uchar4 sample_px(const ResampleArgs &a, float u, float v) {
+    int y, cb, cr;
+    sample_ycbcr(a, u, v, y, cb, cr);
     return to_rgba(y, cb, cr);
 }
 
-// Two horizontally adjacent pixels (i, j), (i + 1, j) per thread
-// (independent work for the scheduler to overlap), written with one 8-byte
-// store when aligned.
 // Luma / 255, Cb and Cr of viewport pixel (i, j) into the planes.
 __device__ __forceinline__ void sample_ycc(const ResampleArgs &a, int i, int j) {
     float u, v;
     project_px(a.v, i, j, u, v);
-    const int y = bilinear_u8(a.plane[0], a.w[0], a.h[0], u, v);
-    int cb = 128, cr = 128;
-    if (a.planes == 3) {
-        float uc = u, vc = v;
-        if (a.c420) {
-            uc = fmaf(u + 0.5f, 0.5f, -0.5f);
-            vc = fmaf(v + 0.5f, 0.5f, -0.5f);
-        }
-        cb = bilinear_u8(a.plane[1], a.w[1], a.h[1], uc, vc);
-        cr = bilinear_u8(a.plane[2], a.w[2], a.h[2], uc, vc);
-    }
+    int y, cb, cr;
+    sample_ycbcr(a, u, v, y, cb, cr);
     const size_t o = (size_t)j * a.v.out_w + i;
     a.y_plane[o] = (float)y * (1.0f / 255.0f);
     a.cb_plane[o] = (uint8_t)cb;
     a.cr_plane[o] = (uint8_t)cr;
 }
 
+// Two horizontally adjacent pixels (i, j), (i + 1, j) per thread
+// (independent work for the scheduler to overlap), written with one 8-byte
+// store when aligned.
 __device__ __forceinline__ void resample_pair(const ResampleArgs &a, int i, int j) {
     if (i >= a.v.out_w || j >= a.v.out_h) return;
     if (a.y_plane) {
