@@ -65,6 +65,23 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def job_throughput(ms_local: float, units_local: float, world: int, device=None):
+    """Whole-job timing over ranks: the slowest rank's duration (ms) and the
+    units all ranks processed; returns (ms, units, units per second).  Ranks
+    are replicas (no collective on the data path); this is the only
+    cross-rank exchange, after the timed region."""
+    ms, units = float(ms_local), float(units_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t_ms = torch.tensor([ms], dtype=torch.float64, device=device)
+        t_n = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t_n, op=dist.ReduceOp.SUM)
+        ms, units = float(t_ms.item()), float(t_n.item())
+    return ms, units, units / (ms / 1e3)
+
+
 def workload(size):
     import synth
     frames = synth.equirect_gop(size, FRAMES, seed=2, n_discs=50)
@@ -564,14 +581,7 @@ def run_ours(args):
             step()
         t1.record(stream)
         barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    n_view = args.steps * len(poses) * world
-    value = n_view / (ms / 1e3)
+    ms, n_view, value = job_throughput(t0.elapsed_time(t1), args.steps * len(poses), world, dev)
     if s.sync_status() != 0:
         raise RuntimeError("device error during the timed region")
 
