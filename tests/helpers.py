@@ -57,6 +57,18 @@ def _wide_frames(n, seed):
     return [tuple(np.ascontiguousarray(p[: p.shape[0] // 2]) for p in f) for f in fr]
 
 
+# one wavelet level (the fused single pass), small non-square frames
+CASES["l1_53"] = (lambda: [tuple(np.ascontiguousarray(pl[:64, :128]) for pl in f)
+                           for f in synth.equirect_gop(128, 2, seed=51, n_discs=3)],
+                  O.Params(128, 64, 3, 1, 1, O.WAVELET_53, 2, 1, 16, 1.0))
+CASES["l1_97"] = (lambda: [tuple(np.ascontiguousarray(pl[:64, :128]) for pl in f)
+                           for f in synth.equirect_gop(128, 2, seed=52, n_discs=3)],
+                  O.Params(128, 64, 3, 1, 1, O.WAVELET_97, 2, 1, 16, 3.0))
+# a constant frame: every detail block is zero and omitted from the stream
+CASES["flat97"] = (lambda: [(np.full((128, 128), 77, np.uint8),)] * 2,
+                   O.Params(128, 128, 1, 0, 3, O.WAVELET_97, 2, 1, 32, 4.0))
+
+
 @functools.lru_cache(maxsize=None)
 def case(name: str):
     """(frames, params, stream bytes, oracle Stream) of a named workload."""
@@ -148,3 +160,24 @@ def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v):
     Cbx = np.tile(Cb, (1, m))
     Crx = np.tile(Cr, (1, m))
     return O.ycbcr_to_rgba(Yx, Cbx, Crx), flag
+
+
+def viewport_mismatches(ref, p: O.Params, got: np.ndarray, yaw, pitch, fov):
+    """Compare a GPU viewport (h, w, 4) with the oracle planes `ref` (list of
+    (x, u8)): a pixel passes when it equals the oracle's value at one of the
+    1/256 positions within the float32 error bound of its fp64 position (for
+    9/7 also with the other rounding of near-half samples).  Returns (bad,
+    excused) pixel counts; excused pixels need more than four quanta per axis."""
+    oh, ow = got.shape[:2]
+    planes = [u8 for (_, u8) in ref]
+    u, v = O.project(ow, oh, yaw, pitch, fov, p.width, p.height)
+    eu, ev = position_error_bound(p, ow, oh, yaw, pitch, fov)
+    u, v, eu, ev = u.ravel(), v.ravel(), eu.ravel(), ev.ravel()
+    g = got.reshape(-1, 4)
+    cand, flag = rgba_candidates(planes, p, u, v, eu, ev)
+    ok = np.any(np.all(cand == g[:, None, :], axis=-1), axis=-1)
+    if p.wavelet == O.WAVELET_97:
+        alt = [other_rounding(x) for (x, _) in ref]
+        cand2, _ = rgba_candidates(alt, p, u, v, eu, ev)
+        ok |= np.any(np.all(cand2 == g[:, None, :], axis=-1), axis=-1)
+    return int(np.sum(~ok & ~flag)), int(np.sum(flag))
