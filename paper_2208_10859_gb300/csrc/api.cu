@@ -33,6 +33,19 @@ enum Kernel { kKFootprint = 0, kKTiles = 1, kKCoarse = 2, kKFine = 3, kKResample
 
 bool split_mode(const wv_stream *s) { return s->decode_mode == 0 && s->g.levels >= 3; }
 
+// Coefficient frames of `frame` with the byte quantiser's parameters of the
+// paper-faithful format (quant 1).
+Bands stream_bands(const wv_stream *s, int frame) {
+    Bands b = frame_bands(s->g, frame);
+    if (s->g.quant == 1)
+        for (int k = 0; k < b.n; ++k)
+            for (int p = 0; p < 3; ++p)
+                for (int c = 0; c < 2; ++c)
+                    for (int e = 0; e < 2; ++e)
+                        b.qp[k][p][c][e] = s->qp_host[(((size_t)b.t[k] * 3 + p) * 2 + c) * 2 + e];
+    return b;
+}
+
 // Generation stamp of the next viewport (0 is never used: the stamp arrays
 // start zeroed).
 uint32_t next_gen(wv_stream *s) {
@@ -178,7 +191,7 @@ namespace wv {
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h) {
     const Geom &g = s->g;
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
-    const Bands b = frame_bands(g, frame);
+    const Bands b = stream_bands(s, frame);
     const uint32_t gen = next_gen(s);
     prof_begin(s, kKFootprint);
     launch_footprint(g, v, s->mask, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
@@ -326,7 +339,9 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     if (d.tlevels < 0 || d.tlevels > kMaxBands - 1) return WV_ERR_ARG;
     if (d.num_frames < 1 || d.num_frames % (1 << d.tlevels)) return WV_ERR_ARG;
     if (d.block < 16 || d.block > 256 || (d.block & (d.block - 1))) return WV_ERR_ARG;
-    if (d.quant != 0 || !(d.step > 0.f) || !isfinite(d.step)) return WV_ERR_ARG;
+    if (d.quant != 0 && d.quant != 1) return WV_ERR_ARG;
+    if (d.quant == 1 && (d.wavelet != WV_WAVELET_97 || d.block != 32)) return WV_ERR_ARG;
+    if (!(d.step > 0.f) || !isfinite(d.step)) return WV_ERR_ARG;
     if (d.wavelet == WV_WAVELET_53 && (d.step != floorf(d.step) || d.step > 65536.f))
         return WV_ERR_ARG;
     if (d.width < 2 || d.height < 2 || d.width > 16384 || d.height > 16384) return WV_ERR_ARG;
@@ -341,6 +356,7 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     g->log2b = 0;
     while ((1 << g->log2b) < d.block) ++g->log2b;
     g->step = d.step;
+    g->quant = d.quant;
     g->cells_x = d.width / kCell;
     g->cells_y = d.height / kCell;
     g->tile = tile;
@@ -386,6 +402,7 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
 
 Bands frame_bands(const Geom &g, int frame) {
     Bands b;
+    memset(&b, 0, sizeof(b));
     const int k = g.tlevels, n = 1 << k;
     const int set = frame / n, fl = frame % n;
     b.n = 1 + k;
@@ -463,6 +480,18 @@ const char *wv_strerror(int code) {
 int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc, size_t *device_bytes) {
     wv_stream_desc d;
     StreamHeader h;
+    if (is_paper_stream(bytes, n)) {
+        PaperInfo info;
+        const int rc = paper_parse(bytes, n, &d, &info);
+        if (rc != WV_OK) return rc;
+        if (desc) *desc = d;
+        if (device_bytes) {
+            Geom g;
+            build_geom(d, &g);
+            *device_bytes = layout(g, info.n_slots).total;
+        }
+        return WV_OK;
+    }
     const int rc = parse(bytes, n, &d, &h);
     if (rc != WV_OK) return rc;
     if (desc) *desc = d;
@@ -480,8 +509,14 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     *out = nullptr;
     wv_stream_desc d;
     StreamHeader h;
-    int rc = parse(bytes, n, &d, &h);
+    PaperInfo paper;
+    const bool is_paper = is_paper_stream(bytes, n);
+    int rc = is_paper ? paper_parse(bytes, n, &d, &paper) : parse(bytes, n, &d, &h);
     if (rc != WV_OK) return rc;
+    if (is_paper) {
+        memset(&h, 0, sizeof(h));
+        h.n_payload = paper.n_slots;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return WV_ERR_CUDA;
     wv_stream *s = new (std::nothrow) wv_stream();
@@ -525,10 +560,17 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     s->err = (int *)(base + L.err);
     const size_t tcount = (size_t)s->g.num_frames * s->g.nbpf;
     s->table_host.resize(tcount);
-    memcpy(s->table_host.data(), (const char *)bytes + h.table_off, tcount * 4);
+    if (is_paper) {
+        memcpy(s->table_host.data(), paper.table.data(), tcount * 4);
+        s->qp_host = paper.qp;
+    } else {
+        memcpy(s->table_host.data(), (const char *)bytes + h.table_off, tcount * 4);
+    }
     cudaError_t e = cudaMemcpyAsync(s->table, s->table_host.data(), tcount * 4,
                                     cudaMemcpyHostToDevice, s->cs);
-    if (e == cudaSuccess && h.n_payload)
+    if (e == cudaSuccess && is_paper)
+        e = paper_transcode(bytes, n, paper, s->payload, s->cs);
+    else if (e == cudaSuccess && h.n_payload)
         e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
                             h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
@@ -575,7 +617,7 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
     }
     launch_all_tiles(g, plane, s->tiles, s->counters, s->cs);
     if (split_mode(s)) launch_all_ctiles(g, plane, s->ctiles, s->counters, s->cs);
-    cudaError_t e = run_decode(s, frame_bands(g, frame), outs, f32, as_float ? plane : -1);
+    cudaError_t e = run_decode(s, stream_bands(s, frame), outs, f32, as_float ? plane : -1);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     return cuda_err(cudaGetLastError());
 }
@@ -699,7 +741,7 @@ int wv_set_decode_mode(wv_stream *s, int mode) {
 }
 
 int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes, size_t *max_stream_bytes) {
-    if (!desc) return WV_ERR_ARG;
+    if (!desc || desc->quant != 0) return WV_ERR_ARG;   // the GPU encoder writes dead-zone streams
     Geom g;
     if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
     return encode_sizes(g, scratch_bytes, max_stream_bytes);
@@ -707,7 +749,7 @@ int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes, size_t *m
 
 int wv_encode(const wv_stream_desc *desc, const void *const *planes_dev, void *scratch_dev,
               size_t scratch_bytes, void *out, size_t cap, size_t *out_len, void *cuda_stream) {
-    if (!desc || !planes_dev || !scratch_dev || !out || !out_len) return WV_ERR_ARG;
+    if (!desc || !planes_dev || !scratch_dev || !out || !out_len || desc->quant != 0) return WV_ERR_ARG;
     Geom g;
     if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
     return encode_run(g, planes_dev, scratch_dev, scratch_bytes, out, cap, out_len,

@@ -91,6 +91,7 @@ namespace {
 
 int check_request(const wv_request &r) {
     if (!r.s) return WV_ERR_ARG;
+    if (r.s->g.quant != 0) return WV_ERR_ARG;   // the paper-format quantiser has no batched kernel
     if (r.frame < 0 || r.frame >= r.s->g.num_frames) return WV_ERR_ARG;
     if (!(r.fov > 0.f && r.fov < 3.14159f) || !isfinite(r.yaw) || !isfinite(r.pitch)) return WV_ERR_ARG;
     const wv_image *o = &r.out;

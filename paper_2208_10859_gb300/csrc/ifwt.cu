@@ -125,10 +125,33 @@ struct Raw {
     int keep[2];         // foveation: bit 0 keeps coefficients 0-3, bit 1 keeps 4-7
 };
 
-template <int WAV, int NB>
+// QM = 1: the byte quantiser of the paper-faithful format (Sec. 3.3): a
+// stored value v > 0 is code + 1 and decodes to c_min + code (c_max - c_min)
+// / 255 of its coefficient frame, plane and class (cls 0: approximation
+// band, 1: detail bands); 0 is an absent coefficient (0).
+template <int WAV, int NB, int QM = 0>
 __device__ __forceinline__ void combine8(const TileArgs &a, const uint4 *q, const bool *have,
-                                         float s, typename Traits<WAV>::T out[8]) {
-    if constexpr (WAV == 1) {
+                                         float s, int plane, int cls, typename Traits<WAV>::T out[8]) {
+    if constexpr (WAV == 1 && QM == 1) {
+        float acc[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (!have[b] || (q[b].x | q[b].y | q[b].z | q[b].w) == 0) continue;
+            const uint32_t w[4] = {q[b].x, q[b].y, q[b].z, q[b].w};
+            const float sg = (b == 0 || a.bands.bit[b]) ? 1.f : -1.f;
+            const float lo = a.bands.qp[b][plane][cls][0], d = a.bands.qp[b][plane][cls][1];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int v = (m & 1) ? hi16(w[m >> 1]) : lo16(w[m >> 1]);
+                const float c = v ? fmaf((float)(v - 1), d, lo) : 0.f;
+                acc[m] = fmaf(sg, c, acc[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) out[m] = acc[m] * s;
+    } else if constexpr (WAV == 1) {
         float acc[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = 0.f;
@@ -185,8 +208,8 @@ __device__ __forceinline__ bool fovea_kept(const TileArgs &a, const PlaneGeom &p
 }
 
 // Dequantised, rebuilt coefficient (scalar path for edge chunks).
-template <int WAV, int NB, bool FOV>
-__device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, const PlaneGeom &pg,
+template <int WAV, int NB, bool FOV, int QM = 0>
+__device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, const PlaneGeom &pg, int plane,
                                                          int level, int sub, int kx, int ky) {
     const Geom &g = a.g;
     using T = typename Traits<WAV>::T;
@@ -205,7 +228,7 @@ __device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, cons
         q[b] = make_uint4((uint32_t)(uint16_t)v, 0, 0, 0);
     }
     typename Traits<WAV>::T out[8];
-    combine8<WAV, NB>(a, q, have, a.scale[level][sub], out);
+    combine8<WAV, NB, QM>(a, q, have, a.scale[level][sub], plane, sub == 0 ? 0 : 1, out);
     return out[0];
 }
 
@@ -281,7 +304,7 @@ __device__ __forceinline__ void clear_halves(uint4 (&q)[NB], int keep) {
     }
 }
 
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, int QM = 0>
 __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &pg, int plane,
                                             const LevelGeo &G, const Task &t, Raw<NB> &r,
                                             const float *P, int nch, float *A) {
@@ -296,21 +319,21 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
         // odd columns: HL (even row) or HH (odd row)
         if (t.fast) {
             if (FOV && r.keep[1] != 3) clear_halves<NB>(r.q[1], r.keep[1]);
-            combine8<WAV, NB>(a, r.q[1], r.have[1], a.scale[G.l][s_odd], od);
+            combine8<WAV, NB, QM>(a, r.q[1], r.have[1], a.scale[G.l][s_odd], plane, 1, od);
         } else {
 #pragma unroll
             for (int m = 0; m < 8; ++m)
-                od[m] = coef1<WAV, NB, FOV>(a, pg, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
+                od[m] = coef1<WAV, NB, FOV, QM>(a, pg, plane, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
         }
         // even columns: LH (odd row) or LL (even row)
         if (s_even == 2 || G.l == g.levels) {
             if (t.fast) {
                 if (FOV && r.keep[0] != 3) clear_halves<NB>(r.q[0], r.keep[0]);
-                combine8<WAV, NB>(a, r.q[0], r.have[0], a.scale[G.l][s_even], ev);
+                combine8<WAV, NB, QM>(a, r.q[0], r.have[0], a.scale[G.l][s_even], plane, s_even == 0 ? 0 : 1, ev);
             } else {
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
-                    ev[m] = coef1<WAV, NB, FOV>(a, pg, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
+                    ev[m] = coef1<WAV, NB, FOV, QM>(a, pg, plane, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
             }
         } else if (G.l == a.l_top) {   // LL from a plane written by a coarser pass
             const float *src = a.ll_in[plane] + (size_t)t.ky * a.ll_in_pitch[plane];
@@ -404,7 +427,7 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
     }
 }
 
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, int QM = 0>
 __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &pg, int plane, const LevelGeo &G,
                             const float *P, float *A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -435,8 +458,8 @@ __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &
         Raw<NB> r0, r1;
         load_task<WAV, NB, FOV>(a, pg, G, t0, r0);
         load_task<WAV, NB, FOV>(a, pg, G, t1, r1);
-        finish_task<WAV, NB, FOV>(a, pg, plane, G, t0, r0, P, nch, A);
-        finish_task<WAV, NB, FOV>(a, pg, plane, G, t1, r1, P, nch, A);
+        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t0, r0, P, nch, A);
+        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t1, r1, P, nch, A);
     }
 }
 
@@ -594,7 +617,7 @@ __device__ __forceinline__ void column_pair(const float *A, int sa, int col, int
 
 // Decode one tile (entry: plane << 28 | ty << 14 | tx) of a pass: levels
 // l_top down to l_bot; A and P are the CTA's shared arrays.
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, int QM = 0>
 __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float *A, float *P) {
     constexpr int H = Traits<WAV>::H;
     const Geom &g = a.g;
@@ -620,7 +643,7 @@ __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float 
             return;
         }
         // 1. gather + horizontal synthesis into A
-        gather_rows<WAV, NB, FOV>(a, pg, plane, G, P, A);
+        gather_rows<WAV, NB, FOV, QM>(a, pg, plane, G, P, A);
         __syncthreads();
         // 2. vertical synthesis of the columns the outputs need
         const int nv = G.ox.hi - G.ox.lo + 1;
@@ -715,13 +738,13 @@ __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float 
     }
 }
 
-template <int WAV, int NB>
+template <int WAV, int NB, int QM>
 __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
     extern __shared__ __align__(16) float smem[];
     float *A = smem;
     float *P = smem + a.a_floats;
     const int count = *(volatile const int *)a.count;
-    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) decode_one<WAV, NB, false>(a, a.tiles[ti], A, P);
+    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) decode_one<WAV, NB, false, QM>(a, a.tiles[ti], A, P);
 }
 
 // ---- batched decode: one persistent launch over all surfaces ---------------
@@ -846,9 +869,12 @@ void fill_tile_scales(TileArgs &a) {
     const double k2 = kK * kK;
     for (int l = 0; l <= kMaxLevels; ++l) {
         if (a.g.wavelet == WV_WAVELET_97) {
-            a.scale[l][0] = (float)(0.5 * a.g.step * pow(k2, a.g.levels));
-            a.scale[l][1] = a.scale[l][2] = (float)(0.5 * a.g.step * pow(k2, l - 1));
-            a.scale[l][3] = (float)(0.5 * a.g.step * pow(k2, l - 2));
+            // dead zone: (2q + sign q) step / 2; byte quantiser: coefficients
+            // of samples / 255, back to 8-bit units
+            const double unit = a.g.quant == 1 ? 255.0 : 0.5 * a.g.step;
+            a.scale[l][0] = (float)(unit * pow(k2, a.g.levels));
+            a.scale[l][1] = a.scale[l][2] = (float)(unit * pow(k2, l - 1));
+            a.scale[l][3] = (float)(unit * pow(k2, l - 2));
         } else {
             a.scale[l][0] = a.scale[l][1] = a.scale[l][2] = a.scale[l][3] = 1.f;
         }
@@ -857,7 +883,7 @@ void fill_tile_scales(TileArgs &a) {
 
 namespace {
 
-template <int WAV, int NB>
+template <int WAV, int NB, int QM = 0>
 cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
     // largest dynamic shared memory opted in so far, per device
     static int opted[64] = {};
@@ -865,11 +891,11 @@ cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) 
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || smem > opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) opted[dev] = smem;
     }
-    k_tiles<WAV, NB><<<grid, threads, smem, cs>>>(a);
+    k_tiles<WAV, NB, QM><<<grid, threads, smem, cs>>>(a);
     return cudaGetLastError();
 }
 
@@ -902,6 +928,14 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
     const int threads = coarse ? kThreads / 2 : kThreads;
     const int grid = decode_tiles_grid(a.g) * (coarse ? 2 : 1);
     const int nb = a.bands.n;
+    if (a.g.quant == 1) {   // paper-faithful byte quantiser (9/7 only)
+        switch (nb) {
+        case 1: return launch_t<1, 1, 1>(a, grid, threads, cs);
+        case 2: return launch_t<1, 2, 1>(a, grid, threads, cs);
+        case 3: return launch_t<1, 3, 1>(a, grid, threads, cs);
+        default: return launch_t<1, 4, 1>(a, grid, threads, cs);
+        }
+    }
     if (a.g.wavelet == WV_WAVELET_97) {
         switch (nb) {
         case 1: return launch_t<1, 1>(a, grid, threads, cs);

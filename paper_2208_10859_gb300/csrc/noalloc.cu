@@ -51,6 +51,7 @@ extern "C" int wv_decode_plane_static(const wv_stream_desc *desc, const void *pa
                                       const void *table_dev, int frame, int plane, void *out_dev,
                                       int as_float, void *cuda_stream) {
     if (!desc || !payload_dev || !table_dev || !out_dev) return WV_ERR_ARG;
+    if (desc->quant != 0) return WV_ERR_ARG;   // the byte quantiser needs per-frame parameters
     wv::Geom g;
     if (wv::build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
     if (frame < 0 || frame >= g.num_frames || plane < 0 || plane >= g.planes) return WV_ERR_ARG;

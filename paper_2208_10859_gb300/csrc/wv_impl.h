@@ -47,6 +47,7 @@ struct PlaneGeom {
 
 struct Geom {
     int planes, c420, levels, wavelet, num_frames, tlevels, block, log2b, nbpf;
+    int quant;   // 0: dead-zone uniform quantiser (step); 1: byte quantiser of the paper format
     float step;
     PlaneGeom p[3];
     int cells_x, cells_y;
@@ -63,6 +64,9 @@ struct Bands {
     int n;
     int t[kMaxBands];
     int bit[kMaxBands];
+    // byte quantiser (quant 1): per band, plane and class (0 approximation,
+    // 1 details) the pair (c_min, (c_max - c_min) / 255)
+    float qp[kMaxBands][3][2][2];
 };
 
 // Viewport camera: ray of pixel (i, j) is R * ((i + 1/2) sx - 1) t,
@@ -188,6 +192,18 @@ struct StreamHeader {
 static_assert(sizeof(StreamHeader) == 88, "stream header layout");
 constexpr size_t kHeaderBytes = 128;
 
+// paper-faithful stream format (paper.cu)
+struct PaperInfo {
+    uint64_t n_slots;              // stored blocks (blocks with records)
+    std::vector<int32_t> table;    // [frame][block] slot or -1
+    std::vector<uint2> src;        // per slot: byte offset of its records, count
+    std::vector<float> qp;         // [frame][3][2][2] (c_min, step) per plane and class
+};
+bool is_paper_stream(const void *bytes, size_t n);
+int paper_parse(const void *bytes, size_t n, wv_stream_desc *d, PaperInfo *info);
+cudaError_t paper_transcode(const void *bytes, size_t n, const PaperInfo &info, int16_t *payload,
+                            cudaStream_t cs);
+
 // host helpers (api.cu)
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h);
 int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
@@ -267,6 +283,7 @@ struct wv_stream {
     int *err = nullptr;
     uint64_t n_payload = 0;
     std::vector<int32_t> table_host;
+    std::vector<float> qp_host;   // byte quantiser parameters (quant 1), [frame][3][2][2]
     // profiling: (kernel id, start, stop) event triples
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;

@@ -98,3 +98,28 @@ def test_null_stream_arguments_are_rejected(lib):
     assert lib.wv_set_decode_mode(None, 0) == -1
     assert lib.wv_decode_viewport(None, 0, 0.0, 0.0, 1.0, None) == -1
     assert lib.wv_stream_sync_status(None) == -1
+
+
+def test_query_parses_and_rejects_paper_streams(lib):
+    import struct
+    import synth
+    from oracle import paper_format as PF
+    from paper_2208_10859_gb300 import wv
+    fr = synth.equirect_gop(64, 4, seed=9, n_discs=2)
+    data = PF.encode(fr, PF.PaperParams(64, 64, 3, 1, 2, 4, 2, alpha=0.0, alpha_t=0.0))
+    desc, need = wv.query(data)
+    assert (desc["quant"], desc["block"], desc["tlevels"], desc["wavelet"]) == (1, 32, 2, 1)
+    assert need > 0
+    off = struct.unpack_from("<Q", data, 128)[0]
+    b = bytearray(data)
+    struct.pack_into("<I", b, off, 10 ** 8)                  # record count past the end
+    bad = [data[:200], bytes(b)]
+    b = bytearray(data)
+    nbpf = struct.unpack_from("<I", data, 40)[0]
+    ends = off + 8 + 16 * 3
+    struct.pack_into("<I", b, ends, 10 ** 6)                 # BlockEnd beyond the record count
+    bad.append(bytes(b))
+    for x in bad:
+        with pytest.raises(wv.WVError) as e:
+            wv.query(x)
+        assert e.value.code == -2

@@ -1,0 +1,79 @@
+"""GPU decoding of the paper-faithful format (Sec. 3.3, 3.4): streams the
+oracle encodes (Eq. 3 thresholds, byte quantiser, sparse records with
+BlockEnd pointers, inter-frame sets of four transformed to the last level)
+decode on the GPU to the oracle's samples within the float tolerance, and
+their viewports match the oracle's candidates."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import paper_format as PF
+import synth
+import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = {
+    "yuv": (lambda: synth.equirect_gop(256, 4, seed=61, n_discs=6),
+            PF.PaperParams(256, 256, 3, 1, 4, 4, 2, alpha=0.05, alpha_t=0.005)),
+    "grey_small_alpha": (lambda: synth.equirect_gop(128, 8, seed=62, n_discs=4, chroma=False),
+                         PF.PaperParams(128, 128, 1, 0, 3, 8, 2, alpha=0.0, alpha_t=0.0)),
+}
+
+
+def _case(name):
+    build, pp = CASES[name]
+    frames = build()
+    data = PF.encode(frames, pp)
+    return frames, pp, data, PF.PaperStream(data)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_planes_match_oracle(name):
+    from paper_2208_10859_gb300 import wv
+    _, pp, data, st = _case(name)
+    s = wv.Stream(data)
+    assert s.desc["quant"] == 1 and s.desc["block"] == 32
+    for f in range(pp.num_frames):
+        for pl in range(pp.planes):
+            x, u8 = st.decode_plane(f, pl)
+            w, h = x.shape[1], x.shape[0]
+            of = torch.empty((h, w), dtype=torch.float32, device="cuda")
+            s.decode_full(f, pl, of, as_float=True)
+            ob = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+            s.decode_full(f, pl, ob)
+            torch.cuda.synchronize()
+            err = np.abs(of.cpu().numpy().astype(np.float64) - x)
+            assert err.max() <= H.tol_97_levels(), (f, pl, err.max())
+            diff = ob.cpu().numpy() != u8
+            assert not np.any(diff & ~H.near_half(x))
+    assert s.sync_status() == 0
+
+
+def test_viewports_match_oracle():
+    from paper_2208_10859_gb300 import wv
+    _, pp, data, st = _case("yuv")
+    s = wv.Stream(data)
+    p = pp.codec()
+    for k, (yaw, pitch, fov) in enumerate([(0.2, 0.1, 1.9), (2.8, -0.5, 1.5), (-1.0, 1.3, 1.7)]):
+        frame = k % pp.num_frames
+        out = torch.zeros((72, 88, 4), dtype=torch.uint8, device="cuda")
+        s.decode_viewport(frame, yaw, pitch, fov, out)
+        torch.cuda.synchronize()
+        ref = [st.decode_plane(frame, pl) for pl in range(pp.planes)]
+        bad, exc = H.viewport_mismatches(ref, p, out.cpu().numpy(), yaw, pitch, fov)
+        assert bad == 0 and exc <= 0.01 * 72 * 88
+    assert s.sync_status() == 0
+
+
+def test_batch_refuses_paper_streams():
+    from paper_2208_10859_gb300 import wv
+    _, _, data, _ = _case("grey_small_alpha")
+    s = wv.Stream(data)
+    out = torch.zeros((8, 8, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(wv.WVError) as e:
+        wv.decode_batch([wv.ViewRequest(s, 0, 0.0, 0.0, 1.0, out)])
+    assert e.value.code == -1
