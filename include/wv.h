@@ -62,7 +62,9 @@ extern "C" {
  * by 2^levels.  The inter-frame set holds 2^tlevels frames (Sec. 3.2);
  * num_frames is a multiple of it.  block is the side of the square
  * coefficient blocks (a power of two, 16..256).  quant 0 = dead-zone uniform
- * quantiser with step `step` (integer >= 1 for 5/3). */
+ * quantiser with step `step` (integer >= 1 for 5/3); quant 1 = the byte
+ * quantiser of the paper-faithful format (9/7, block 32; streams "WVP1",
+ * see wv_encode_paper). */
 typedef struct {
     int width, height;
     int planes;        /* 1 (grey) or 3 (Y, Cb, Cr) */
@@ -518,6 +520,24 @@ int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes,
 int wv_encode(const wv_stream_desc *desc, const void *const *planes_dev,
               void *scratch_dev, size_t scratch_bytes, void *out, size_t cap,
               size_t *out_len, void *cuda_stream);
+
+/* Encode into the paper-faithful format ("WVP1", Sec. 3.3 / 3.4) on the GPU.
+ * desc: quant = 1, wavelet = 9/7, block = 32 (width, height, planes,
+ * chroma_420, levels, num_frames, tlevels as for wv_encode; step unused).
+ * Samples are normalised to [0, 1] around 128; after the frame-wise FWT every
+ * coefficient with |W| <= alpha ((l_max - l) / l_max)^2 + H(y) is dropped
+ * (Eq. 3; H(y) = 1 - sin(pi y / S_y), Sec. 3.6, y the row inside the
+ * subband; the approximation band uses l = l_max); after the inter-frame Haar
+ * (sets of 2^tlevels frames, to the last level) the same with alpha_t and the
+ * temporal level; the survivors of each coefficient frame, plane and class
+ * (approximation band / detail bands) are quantised to one byte between
+ * their extremes.  Output: header, per-frame offsets, per coefficient frame
+ * the extremes, the BlockEnd pointers of the 32 x 32 blocks and the records
+ * (index in the block | byte << 16).  Scratch and capacity from
+ * wv_encode_sizes with the same desc.  Synchronises cuda_stream. */
+int wv_encode_paper(const wv_stream_desc *desc, const void *const *planes_dev, void *scratch_dev,
+                    size_t scratch_bytes, float alpha, float alpha_t, void *out, size_t cap,
+                    size_t *out_len, void *cuda_stream);
 
 #ifdef __cplusplus
 }

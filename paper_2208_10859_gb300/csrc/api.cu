@@ -741,7 +741,7 @@ int wv_set_decode_mode(wv_stream *s, int mode) {
 }
 
 int wv_encode_sizes(const wv_stream_desc *desc, size_t *scratch_bytes, size_t *max_stream_bytes) {
-    if (!desc || desc->quant != 0) return WV_ERR_ARG;   // the GPU encoder writes dead-zone streams
+    if (!desc) return WV_ERR_ARG;
     Geom g;
     if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
     return encode_sizes(g, scratch_bytes, max_stream_bytes);
@@ -754,6 +754,17 @@ int wv_encode(const wv_stream_desc *desc, const void *const *planes_dev, void *s
     if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
     return encode_run(g, planes_dev, scratch_dev, scratch_bytes, out, cap, out_len,
                       (cudaStream_t)cuda_stream);
+}
+
+int wv_encode_paper(const wv_stream_desc *desc, const void *const *planes_dev, void *scratch_dev,
+                    size_t scratch_bytes, float alpha, float alpha_t, void *out, size_t cap, size_t *out_len,
+                    void *cuda_stream) {
+    if (!desc || !planes_dev || !scratch_dev || !out || !out_len || desc->quant != 1) return WV_ERR_ARG;
+    if (!(alpha >= 0.f) || !(alpha_t >= 0.f) || !isfinite(alpha) || !isfinite(alpha_t)) return WV_ERR_ARG;
+    Geom g;
+    if (build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
+    return encode_paper(g, planes_dev, scratch_dev, scratch_bytes, alpha, alpha_t, out, cap, out_len,
+                        (cudaStream_t)cuda_stream);
 }
 
 }  // extern "C"

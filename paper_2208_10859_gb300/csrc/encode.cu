@@ -186,7 +186,10 @@ ScratchLayout scratch_layout(const Geom &g) {
     s.misc = o;   // err, plane widths, plane offsets, coef frame pointers
     o = al(o + 4096 + (size_t)g.num_frames * sizeof(void *));
     s.payload = o;
-    o = al(o + (size_t)g.num_frames * g.nbpf * g.block * g.block * 2);
+    if (g.quant == 1)   // paper format: record start per block, then at most one record per coefficient
+        o = al(o + (size_t)g.num_frames * g.nbpf * 8 + (size_t)g.num_frames * s.coef_frame_elems * 4);
+    else
+        o = al(o + (size_t)g.num_frames * g.nbpf * g.block * g.block * 2);
     s.total = o;
     return s;
 }
@@ -332,15 +335,345 @@ int run(const Geom &g, const void *const *planes, char *base, const ScratchLayou
     return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
 }
 
+// ---- paper-faithful format (Sec. 3.3, 3.4) ---------------------------------
+
+// Subband level (LL_L: levels) and the row inside the subband, with its
+// height, of Mallat position (x, y) of a w x h plane.
+__device__ __forceinline__ void subband_of(int x, int y, int w, int h, int levels, int &lev, int &ysub,
+                                           int &sh) {
+    for (int l = 1; l <= levels; ++l) {
+        if (x >= (w >> l) || y >= (h >> l)) {
+            lev = l;
+            sh = h >> l;
+            ysub = y >= sh ? y - sh : y;
+            return;
+        }
+    }
+    lev = levels;
+    sh = h >> levels;
+    ysub = y;
+}
+
+// Eq. 3 with the mapping factor H(y) = 1 - sin(pi y / S_y) (Sec. 3.6); the
+// approximation band uses l = l_max (H only).
+__device__ __forceinline__ float paper_threshold(float alpha, int l, int L, int ysub, int sh) {
+    const float r = (float)(L - l) / (float)L;
+    return alpha * r * r + 1.0f - sinpif((float)ysub / (float)sh);
+}
+
+__global__ void k_load_unit(const uint8_t *src, float *dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = ((float)src[i] - 128.0f) * (1.0f / 255.0f);
+}
+
+__global__ void k_threshold(float *c, int w, int h, int levels, float alpha) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)w * h) return;
+    const int x = (int)(i % w), y = (int)(i / w);
+    int lev, ysub, sh;
+    subband_of(x, y, w, h, levels, lev, ysub, sh);
+    const bool ll = x < (w >> levels) && y < (h >> levels);
+    if (!(fabsf(c[i]) > paper_threshold(alpha, ll ? levels : lev, levels, ysub, sh))) c[i] = 0.f;
+}
+
+// Ordered-integer image of a float (monotonic), for atomic min / max.
+__device__ __forceinline__ int ord(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float unord(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7FFFFFFF); }
+
+// Float inter-frame Haar over the set's n planes (slot order), the
+// inter-frame threshold per slot (temporal level j; the low band as level k),
+// and the extremes of the survivors per slot and class: ext[slot][class][0 min, 1 max].
+__global__ void k_haar_paper(float *work, size_t plane_elems, int k, int w, int h, int levels, float alpha_t,
+                             int *ext) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < (size_t)w * h;
+    const int n = 1 << k;
+    float low[8], bands[8];
+    int lev = 0, ysub = 0, sh = 1;
+    bool ll = false;
+    if (valid) {
+        for (int j = 0; j < n; ++j) low[j] = work[(size_t)j * plane_elems + i];
+        const int x = (int)(i % w), y = (int)(i / w);
+        subband_of(x, y, w, h, levels, lev, ysub, sh);
+        ll = x < (w >> levels) && y < (h >> levels);
+    }
+    int cnt = n, slot_end = n;
+    int slot_level[8];
+    slot_level[0] = k;
+    for (int j = 1; j <= k; ++j) {
+        const int half = cnt / 2;
+        slot_end -= half;
+        for (int m = 0; m < half; ++m) {
+            if (valid) {
+                const float a = low[2 * m], b = low[2 * m + 1];
+                bands[slot_end + m] = (b - a) * 0.5f;
+                low[m] = (a + b) * 0.5f;
+            }
+            slot_level[slot_end + m] = j;
+        }
+        cnt = half;
+    }
+    if (valid) bands[0] = low[0];
+    for (int s = 0; s < n; ++s) {
+        float c = 0.f;
+        if (valid) {
+            c = bands[s];
+            const float r = k > 0 ? (float)(k - slot_level[s]) / (float)k : 0.f;
+            const float T = alpha_t * r * r + 1.0f - sinpif((float)ysub / (float)sh);
+            if (!(fabsf(c) > T)) c = 0.f;
+            work[(size_t)s * plane_elems + i] = c;
+        }
+        // extremes of the survivors: warp-level min / max per class, then atomics
+        for (int cls = 0; cls < 2; ++cls) {
+            const bool mine = valid && c != 0.f && (cls == 0) == ll;
+            int mn = mine ? ord(c) : 0x7FFFFFFF, mx = mine ? ord(c) : (int)0x80000000;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if ((threadIdx.x & 31) == 0 && mn <= mx) {
+                atomicMin(ext + (s * 2 + cls) * 2, mn);
+                atomicMax(ext + (s * 2 + cls) * 2 + 1, mx);
+            }
+        }
+    }
+}
+
+// Byte codes (stored as code + 1; 0 = dropped) of one slot's plane.
+__global__ void k_codes(const float *c, int w, int h, int levels, const int *ext, int16_t *out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)w * h) return;
+    const float v = c[i];
+    if (v == 0.f) {
+        out[i] = 0;
+        return;
+    }
+    const int x = (int)(i % w), y = (int)(i / w);
+    const int cls = (x < (w >> levels) && y < (h >> levels)) ? 0 : 1;
+    const float lo = unord(ext[cls * 2]), hi = unord(ext[cls * 2 + 1]);
+    int code = 0;
+    if (hi > lo) code = min(max(__float2int_rd((v - lo) / (hi - lo) * 255.0f + 0.5f), 0), 255);
+    out[i] = (int16_t)(code + 1);
+}
+
+__global__ void k_block_counts(int16_t *const *coef, const BlockDesc *desc, const int *plane_w,
+                               const size_t *plane_off, int nbpf, int *counts) {
+    const int t = blockIdx.y, b = blockIdx.x;
+    const BlockDesc d = desc[b];
+    const int16_t *c = coef[t] + plane_off[d.plane];
+    const int w = plane_w[d.plane];
+    int n = 0;
+    for (int idx = threadIdx.x; idx < d.bw * d.bh; idx += blockDim.x) {
+        const int y = idx / d.bw, x = idx % d.bw;
+        n += c[(size_t)(d.y0 + y) * w + d.x0 + x] != 0;
+    }
+    __shared__ int sum;
+    if (threadIdx.x == 0) sum = 0;
+    __syncthreads();
+    atomicAdd(&sum, n);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[t * nbpf + b] = sum;
+}
+
+// Records of one block (1024 threads, thread = row-major element): order-
+// preserving compaction with ballots and a scan of the 32 warp counts.
+__global__ void __launch_bounds__(1024) k_records(int16_t *const *coef, const BlockDesc *desc, const int *plane_w,
+                                                  const size_t *plane_off, int nbpf, const long long *start,
+                                                  uint32_t *recs) {
+    const int t = blockIdx.y, b = blockIdx.x;
+    const BlockDesc d = desc[b];
+    const int16_t *c = coef[t] + plane_off[d.plane];
+    const int w = plane_w[d.plane];
+    const int idx = threadIdx.x, y = idx >> 5, x = idx & 31;
+    const int v = (x < d.bw && y < d.bh) ? c[(size_t)(d.y0 + y) * w + d.x0 + x] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
+    __shared__ int wc[32], wo[32];
+    if ((idx & 31) == 0) wc[idx >> 5] = __popc(bal);
+    __syncthreads();
+    if (idx == 0) {
+        int o = 0;
+        for (int k = 0; k < 32; ++k) {
+            wo[k] = o;
+            o += wc[k];
+        }
+    }
+    __syncthreads();
+    if (v != 0) {
+        const long long pos = start[t * nbpf + b] + wo[idx >> 5] + __popc(bal & ((1u << (idx & 31)) - 1u));
+        recs[pos] = (uint32_t)(y * 32 + x) | ((uint32_t)(v - 1) << 16);
+    }
+}
+
+int run_paper(const Geom &g, const void *const *planes, char *base, const ScratchLayout &S, float alpha,
+              float alpha_t, void *out, size_t cap, size_t *out_len, cudaStream_t cs) {
+    const int n = 1 << g.tlevels;
+    float *work = (float *)(base + S.work);
+    float *tmp = (float *)(base + S.tmp);
+    int16_t *coef = (int16_t *)(base + S.coef);
+    int *counts = (int *)(base + S.flags);
+    BlockDesc *desc = (BlockDesc *)(base + S.desc);
+    int *ext = (int *)(base + S.misc);           // [8 slots][2][2] per (set, plane) pass
+    int *plane_w = (int *)(base + S.misc + 512);
+    size_t *plane_off = (size_t *)(base + S.misc + 576);
+    int16_t **coef_ptrs = (int16_t **)(base + S.misc + 4096);
+    long long *start = (long long *)(base + S.payload);
+    uint32_t *recs = (uint32_t *)(base + S.payload + (size_t)g.num_frames * g.nbpf * 8);
+
+    const std::vector<BlockDesc> bd = block_descs(g);
+    if ((int)bd.size() != g.nbpf) return WV_ERR_ARG;
+    std::vector<int16_t *> cptr(g.num_frames);
+    for (int t = 0; t < g.num_frames; ++t) cptr[t] = coef + (size_t)t * S.coef_frame_elems;
+    int pw[3] = {0, 0, 0};
+    size_t poff[3] = {0, 0, 0};
+    size_t acc = 0;
+    for (int p = 0; p < g.planes; ++p) {
+        pw[p] = g.p[p].w;
+        poff[p] = acc;
+        acc += (size_t)g.p[p].w * g.p[p].h;
+    }
+    cudaError_t e = cudaMemcpyAsync(desc, bd.data(), bd.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plane_w, pw, sizeof(pw), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plane_off, poff, sizeof(poff), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(coef_ptrs, cptr.data(), cptr.size() * sizeof(void *), cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    // extremes (c_min, c_max) per coefficient frame, plane, class
+    std::vector<float> ext_host((size_t)g.num_frames * g.planes * 4, 0.f);
+    for (int set = 0; set < g.num_frames / n && e == cudaSuccess; ++set) {
+        for (int p = 0; p < g.planes && e == cudaSuccess; ++p) {
+            const int w = g.p[p].w, h = g.p[p].h;
+            const size_t ne = (size_t)w * h;
+            const unsigned blocks = (unsigned)((ne + 255) / 256);
+            for (int j = 0; j < n; ++j) {
+                const uint8_t *src = (const uint8_t *)planes[(size_t)(set * n + j) * g.planes + p];
+                if (!src) return WV_ERR_ARG;
+                float *wj = work + (size_t)j * S.plane_elems_max;
+                k_load_unit<<<blocks, 256, 0, cs>>>(src, wj, ne);
+                e = transform_plane<float>(wj, tmp, w, h, g.levels, WV_WAVELET_97, cs);
+                if (e != cudaSuccess) break;
+                k_threshold<<<blocks, 256, 0, cs>>>(wj, w, h, g.levels, alpha);
+            }
+            std::vector<int> init(8 * 4);
+            for (int q = 0; q < 8 * 2; ++q) {
+                init[2 * q] = 0x7FFFFFFF;
+                init[2 * q + 1] = (int)0x80000000;
+            }
+            e = cudaMemcpyAsync(ext, init.data(), init.size() * 4, cudaMemcpyHostToDevice, cs);
+            if (e != cudaSuccess) break;
+            k_haar_paper<<<blocks, 256, 0, cs>>>(work, S.plane_elems_max, g.tlevels, w, h, g.levels, alpha_t, ext);
+            for (int sl = 0; sl < n; ++sl)
+                k_codes<<<blocks, 256, 0, cs>>>(work + (size_t)sl * S.plane_elems_max, w, h, g.levels, ext + sl * 4,
+                                                cptr[set * n + sl] + poff[p]);
+            std::vector<int> eh(8 * 4);
+            e = cudaMemcpyAsync(eh.data(), ext, eh.size() * 4, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+            if (e != cudaSuccess) break;
+            auto unord_h = [](int o) {
+                const int b = o >= 0 ? o : o ^ 0x7FFFFFFF;
+                float f;
+                memcpy(&f, &b, 4);
+                return f;
+            };
+            for (int sl = 0; sl < n; ++sl)
+                for (int cls = 0; cls < 2; ++cls) {
+                    const int mn = eh[(sl * 2 + cls) * 2], mx = eh[(sl * 2 + cls) * 2 + 1];
+                    float *dst = &ext_host[(((size_t)(set * n + sl)) * g.planes + p) * 4 + cls * 2];
+                    if (mn <= mx) {
+                        dst[0] = unord_h(mn);
+                        dst[1] = unord_h(mx);
+                    }
+                }
+        }
+    }
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    k_block_counts<<<dim3(g.nbpf, g.num_frames), 256, 0, cs>>>(coef_ptrs, desc, plane_w, plane_off, g.nbpf, counts);
+    std::vector<int> cnt((size_t)g.num_frames * g.nbpf);
+    e = cudaMemcpyAsync(cnt.data(), counts, cnt.size() * 4, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    // layout: header, frame offsets, per frame: count, 0, extremes, BlockEnd, records (16-byte padded)
+    std::vector<long long> st(cnt.size());
+    std::vector<size_t> foff(g.num_frames);
+    std::vector<uint32_t> fcount(g.num_frames);
+    long long total_recs = 0;
+    size_t o = kHeaderBytes + 8 * (size_t)g.num_frames;
+    o = (o + 15) & ~size_t(15);
+    for (int t = 0; t < g.num_frames; ++t) {
+        foff[t] = o;
+        long long c = 0;
+        for (int b = 0; b < g.nbpf; ++b) {
+            st[(size_t)t * g.nbpf + b] = total_recs + c;
+            c += cnt[(size_t)t * g.nbpf + b];
+        }
+        fcount[t] = (uint32_t)c;
+        total_recs += c;
+        o += 8 + 16 * (size_t)g.planes + 4 * (size_t)g.nbpf + 4 * (size_t)c;
+        o = (o + 15) & ~size_t(15);
+    }
+    *out_len = o;
+    if (cap < o) return WV_ERR_OOM;
+    if ((size_t)total_recs * 4 + (size_t)g.num_frames * g.nbpf * 8 > S.total - S.payload) return WV_ERR_OOM;
+    e = cudaMemcpyAsync(start, st.data(), st.size() * 8, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) {
+        k_records<<<dim3(g.nbpf, g.num_frames), 1024, 0, cs>>>(coef_ptrs, desc, plane_w, plane_off, g.nbpf, start, recs);
+        e = cudaGetLastError();
+    }
+    std::vector<uint32_t> rh((size_t)total_recs);
+    if (e == cudaSuccess && total_recs)
+        e = cudaMemcpyAsync(rh.data(), recs, rh.size() * 4, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    char *ob = (char *)out;
+    memset(ob, 0, o);
+    uint32_t hdr[11] = {1, (uint32_t)g.p[0].w, (uint32_t)g.p[0].h, (uint32_t)g.planes, (uint32_t)g.c420,
+                        (uint32_t)g.levels, (uint32_t)g.num_frames, (uint32_t)g.tlevels, 32u, (uint32_t)g.nbpf, 0};
+    memcpy(ob, "WVP1", 4);
+    memcpy(ob + 4, hdr, 10 * 4);
+    memcpy(ob + 44, &alpha, 4);
+    memcpy(ob + 48, &alpha_t, 4);
+    for (int t = 0; t < g.num_frames; ++t) {
+        const uint64_t off = foff[t];
+        memcpy(ob + kHeaderBytes + 8 * t, &off, 8);
+        char *f = ob + off;
+        memcpy(f, &fcount[t], 4);
+        memcpy(f + 8, &ext_host[(size_t)t * g.planes * 4], 16 * (size_t)g.planes);
+        uint32_t *ends = (uint32_t *)(f + 8 + 16 * g.planes);
+        uint32_t c = 0;
+        for (int b = 0; b < g.nbpf; ++b) {
+            c += (uint32_t)cnt[(size_t)t * g.nbpf + b];
+            ends[b] = c;
+        }
+        if (fcount[t])
+            memcpy(f + 8 + 16 * g.planes + 4 * (size_t)g.nbpf, &rh[(size_t)st[(size_t)t * g.nbpf]], 4 * (size_t)fcount[t]);
+    }
+    return WV_OK;
+}
+
 }  // namespace
+
+int encode_paper(const Geom &g, const void *const *planes, void *scratch, size_t scratch_bytes, float alpha,
+                 float alpha_t, void *out, size_t cap, size_t *out_len, cudaStream_t cs) {
+    const ScratchLayout S = scratch_layout(g);
+    if (scratch_bytes < S.total || ((uintptr_t)scratch % 256)) return WV_ERR_OOM;
+    if (g.tlevels > 3 || g.wavelet != WV_WAVELET_97 || g.block != 32) return WV_ERR_ARG;
+    return run_paper(g, planes, (char *)scratch, S, alpha, alpha_t, out, cap, out_len, cs);
+}
 
 int encode_sizes(const Geom &g, size_t *scratch, size_t *max_stream) {
     const ScratchLayout S = scratch_layout(g);
     if (scratch) *scratch = S.total;
     if (max_stream) {
         const size_t tb = (size_t)g.num_frames * g.nbpf * 4;
-        *max_stream = ((kHeaderBytes + tb + 255) & ~size_t(255)) +
-                      (size_t)g.num_frames * g.nbpf * g.block * g.block * 2;
+        if (g.quant == 1)
+            *max_stream = kHeaderBytes + 8 * (size_t)g.num_frames +
+                          (size_t)g.num_frames * (32 + 16 * (size_t)g.planes + tb / g.num_frames) +
+                          (size_t)g.num_frames * S.coef_frame_elems * 4;
+        else
+            *max_stream = ((kHeaderBytes + tb + 255) & ~size_t(255)) +
+                          (size_t)g.num_frames * g.nbpf * g.block * g.block * 2;
     }
     return WV_OK;
 }

@@ -256,6 +256,8 @@ void launch_project(const View &v, float *uv, cudaStream_t cs);
 int encode_sizes(const Geom &g, size_t *scratch, size_t *max_stream);
 int encode_run(const Geom &g, const void *const *planes, void *scratch, size_t scratch_bytes,
                void *out, size_t cap, size_t *out_len, cudaStream_t cs);
+int encode_paper(const Geom &g, const void *const *planes, void *scratch, size_t scratch_bytes, float alpha,
+                 float alpha_t, void *out, size_t cap, size_t *out_len, cudaStream_t cs);
 
 }  // namespace wv
 

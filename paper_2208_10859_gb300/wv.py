@@ -118,6 +118,8 @@ def _lib():
             "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
                                                c_int, vp]),
             "wv_release_default_batch": (None, []),
+            "wv_encode_paper": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, fl, fl, vp, c_size,
+                                        ctypes.POINTER(c_size), vp]),
             "wv_cnn_param_count": (c_size, []),
             "wv_cnn_create": (c_int, [vp, ctypes.POINTER(vp)]),
             "wv_cnn_close": (None, [vp]),
@@ -171,7 +173,7 @@ def exported_symbols() -> list[str]:
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
             "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
-            "wv_cone_bytes_fovea", "wv_request_bytes",
+            "wv_cone_bytes_fovea", "wv_request_bytes", "wv_encode_paper",
             "wv_cnn_param_count", "wv_cnn_create", "wv_cnn_close", "wv_cnn_get_params", "wv_cnn_set_params",
             "wv_cnn_forward", "wv_cnn_gradients", "wv_cnn_train_step", "wv_cnn_sync_status",
             "wv_decode_viewport_filtered",
@@ -419,7 +421,19 @@ class Batch:
             pass
 
 
+def encode_paper(frames, desc: dict, alpha: float, alpha_t: float, cuda_stream=None) -> bytes:
+    """Encode frames (as for encode) into the paper-faithful format on the GPU."""
+    d = dict(desc, quant=1, wavelet=WAVELET_97, block=32, step=1.0)
+    return _encode(frames, d, cuda_stream, lambda L, sd, arr, base, scratch, out, cap, n, cs:
+                   L.wv_encode_paper(sd, arr, base, scratch, alpha, alpha_t, out, cap, n, cs), "wv_encode_paper")
+
+
 def encode(frames, desc: dict, cuda_stream=None) -> bytes:
+    return _encode(frames, desc, cuda_stream, lambda L, sd, arr, base, scratch, out, cap, n, cs:
+                   L.wv_encode(sd, arr, base, scratch, out, cap, n, cs), "wv_encode")
+
+
+def _encode(frames, desc: dict, cuda_stream, call, what) -> bytes:
     """Encode frames (list of num_frames tuples of CUDA uint8 plane tensors) on
     the GPU into stream bytes."""
     import torch
@@ -440,9 +454,9 @@ def encode(frames, desc: dict, cuda_stream=None) -> bytes:
     out = np.empty(cap.value, np.uint8)
     n = ctypes.c_size_t()
     torch.cuda.current_stream().synchronize()
-    _check(_lib().wv_encode(ctypes.byref(d), arr, ctypes.c_void_p(base), scratch.value,
-                            out.ctypes.data_as(ctypes.c_void_p), cap.value, ctypes.byref(n),
-                            ctypes.c_void_p(_cuda_stream_handle(cuda_stream))), "wv_encode")
+    _check(call(_lib(), ctypes.byref(d), arr, ctypes.c_void_p(base), scratch.value,
+                out.ctypes.data_as(ctypes.c_void_p), cap.value, ctypes.byref(n),
+                ctypes.c_void_p(_cuda_stream_handle(cuda_stream))), what)
     del mem, keep
     return out[:n.value].tobytes()
 
