@@ -336,29 +336,33 @@ def serving_leg(args, dev, frames8k, data8k):
         del dfr
     torch.cuda.empty_cache()
     # arrival trace: per headset exponential gaps, random-walk poses
-    rng = np.random.default_rng(11)
-    events = []
-    for h in range(SERVE_HEADSETS):
-        t = float(rng.exponential(1.0 / SERVE_HZ))
-        yaw, pitch = float(rng.uniform(-math.pi, math.pi)), float(rng.uniform(-0.5, 0.5))
-        while t < SERVE_SECONDS + 0.3:
-            yaw += math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal())
-            pitch = float(np.clip(pitch + math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal()), -1.4, 1.4))
-            events.append((t, h, yaw, pitch, int(t * 30) % FRAMES))
-            t += float(rng.exponential(1.0 / SERVE_HZ))
-    events.sort()
+    def trace(headsets, seed):
+        rng = np.random.default_rng(seed)
+        ev = []
+        for h in range(headsets):
+            t = float(rng.exponential(1.0 / SERVE_HZ))
+            yaw, pitch = float(rng.uniform(-math.pi, math.pi)), float(rng.uniform(-0.5, 0.5))
+            while t < SERVE_SECONDS + 0.3:
+                yaw += math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal())
+                pitch = float(np.clip(pitch + math.radians(SERVE_SIGMA_DEG) * float(rng.standard_normal()), -1.4, 1.4))
+                ev.append((t, h, yaw, pitch, int(t * 30) % FRAMES))
+                t += float(rng.exponential(1.0 / SERVE_HZ))
+        ev.sort()
+        return ev
+
     ring = 6
+    max_headsets = 4 * SERVE_HEADSETS
     bufs = [[torch.empty((OUT, OUT, 4), dtype=torch.uint8, device=dev) for _ in range(ring)]
-            for _ in range(SERVE_HEADSETS)]
+            for _ in range(max_headsets)]
     fov = math.radians(FOV_DEG)
 
-    def run(slots, max_batch):
+    def run(slots, max_batch, events, headsets):
         sv = wv.Server(slots=slots, max_batch=max_batch)
         ids = [sv.add_stream(b) for b in blobs]
         for i in range(len(ids)):          # warm: every stream resident, graphs captured
             sv.wait(sv.submit(ids[i], 0, 0.0, 0.0, fov, bufs[0][0]))
-        last = [[None] * ring for _ in range(SERVE_HEADSETS)]
-        count = [0] * SERVE_HEADSETS
+        last = [[None] * ring for _ in range(headsets)]
+        count = [0] * headsets
         warm_end = 0.3
         t0 = time.perf_counter()
         reset = False
@@ -386,10 +390,16 @@ def serving_leg(args, dev, frames8k, data8k):
                 "mean_batch": st["batched_requests"] / max(1, st["batches"]),
                 "slots": slots, "max_batch": max_batch, "offered_per_s": len(lat) / max(1e-9, t_end - warm_end)}
 
-    batching = run(3, 32)
-    plain = run(1, 1)
+    ev32 = trace(SERVE_HEADSETS, 11)
+    batching = run(3, 32, ev32, SERVE_HEADSETS)
+    plain = run(1, 1, ev32, SERVE_HEADSETS)
+    # overload: four times the headsets (about 11.5k requests/s offered)
+    ev128 = trace(max_headsets, 12)
+    batching4 = run(3, 64, ev128, max_headsets)
+    plain4 = run(1, 1, ev128, max_headsets)
     return {"workload": SERVE_WORKLOAD, "budget_ms": SERVE_BUDGET_MS,
-            "continuous_batching": batching, "plain_one_request_per_launch": plain}
+            "continuous_batching": batching, "plain_one_request_per_launch": plain,
+            "overload_128_headsets": {"continuous_batching": batching4, "plain_one_request_per_launch": plain4}}
 
 
 PAPER_ALPHA, PAPER_ALPHA_T, PAPER_LEVELS, PAPER_TLEVELS = 0.1, 0.005, 6, 2
@@ -667,6 +677,32 @@ def run_ours(args):
     trec = traffic_record()
     kernel_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if k != "tiles"}
 
+    # the same 64 viewports through the batch engine (one CUDA graph, one
+    # persistent tile-decode launch): without sharing (every viewport decodes
+    # its own region: the same work as the loop above) and with sharing
+    # (viewports of the same frame decode their common tiles once)
+    engine = {}
+    reqs = [wv.ViewRequest(s, i % FRAMES, yaw, pitch, fov, outs[i]) for i, (yaw, pitch) in enumerate(poses)]
+    for share in (False, True):
+        b = wv.Batch(stream)
+        b.set_sharing(share)
+        for _ in range(args.warmup):
+            b.decode(reqs)
+        barrier()
+        be0, be1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        be0.record(stream)
+        for _ in range(args.steps):
+            b.decode(reqs)
+        be1.record(stream)
+        barrier()
+        if b.sync_status() != 0:
+            raise RuntimeError("device error in the batch engine")
+        st = b.stats()
+        engine["shared_targets" if share else "independent"] = {
+            "viewports_per_s": args.steps * len(poses) / (be0.elapsed_time(be1) / 1e3),
+            "decode_targets": st["surfaces"], "fine_tiles": st["fine_tiles"], "coarse_tiles": st["coarse_tiles"]}
+        b.close()
+
     # end to end through the C ABI with host buffers: upload the coded group
     # from pinned memory (open), decode the 64 viewports, read them back
     pinned_in = torch.from_numpy(np.frombuffer(data, np.uint8)).pin_memory()
@@ -744,6 +780,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg_dec / len(poses),
                          "avg_launch_ms": dec_ms / max(1, dec_n)},
             "kernel_ms_per_launch": kernel_ms,
+            "batch_engine_same_workload": engine,
             "decode_ms_per_viewport": {"split (coarse + fine)": dec_ms / max(1, dec_n),
                                        "fused (all levels per tile)": fused_ms},
             "viewport_bytes": {"cone_coef_mean": sum(cone) / len(cone), "region_mean": sum(region) / len(region),

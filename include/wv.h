@@ -240,6 +240,11 @@ int wv_batch_sync_status(wv_batch *b);
 /* Wait for the last batch and report its statistics. */
 int wv_batch_stats(wv_batch *b, wv_batch_info *info);
 
+/* on = 1 (default): unfoveated requests of the same stream and frame share
+ * one decode target; on = 0: every request decodes its own (the work of
+ * independent wv_decode_viewport calls, scheduled as one batch). */
+int wv_batch_set_sharing(wv_batch *b, int on);
+
 /* on = 1: run batches as direct launches with CUDA events between the steps
  * (wv_batch_stats reports per-step times); on = 0: CUDA graph (default). */
 int wv_batch_set_timing(wv_batch *b, int on);

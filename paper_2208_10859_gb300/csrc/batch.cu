@@ -85,6 +85,7 @@ struct wv_batch {
     // per-step timing of the last launch (direct mode only)
     bool timing = false;
     cudaEvent_t ev[5] = {};
+    bool share = true;                 // unfoveated requests of one (stream, frame) share a surface
 };
 
 namespace {
@@ -115,7 +116,7 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
     P.req_surface.assign(n, -1);
     for (int i = 0; i < n; ++i) {
         const wv_request &r = reqs[i];
-        if (!r.fovea) {
+        if (!r.fovea && b->share) {
             auto it = shared.find({r.s, r.frame});
             if (it != shared.end()) {
                 P.req_surface[i] = it->second;
@@ -522,6 +523,12 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info) {
             info->ms[i] = ms;
         }
     }
+    return WV_OK;
+}
+
+int wv_batch_set_sharing(wv_batch *b, int on) {
+    if (!b || on < 0 || on > 1) return WV_ERR_ARG;
+    b->share = on != 0;
     return WV_OK;
 }
 

@@ -151,6 +151,7 @@ def _lib():
             "wv_batch_sync_status": (c_int, [vp]),
             "wv_batch_stats": (c_int, [vp, ctypes.POINTER(BatchInfo)]),
             "wv_batch_set_timing": (c_int, [vp, c_int]),
+            "wv_batch_set_sharing": (c_int, [vp, c_int]),
             "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int]),
             "wv_batch_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
                                             ctypes.POINTER(c_int)]),
@@ -182,6 +183,7 @@ def exported_symbols() -> list[str]:
             "wv_server_reset_stats", "wv_server_close",
             "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
+            "wv_batch_set_sharing",
             "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
 
 
@@ -395,6 +397,9 @@ class Batch:
 
     def set_timing(self, on: bool) -> None:
         _check(_lib().wv_batch_set_timing(self._h, 1 if on else 0), "wv_batch_set_timing")
+
+    def set_sharing(self, on: bool) -> None:
+        _check(_lib().wv_batch_set_sharing(self._h, 1 if on else 0), "wv_batch_set_sharing")
 
     def set_tile_shape(self, wavelet, levels, width, height, tile, ctile) -> None:
         _check(_lib().wv_batch_set_tile_shape(self._h, wavelet, levels, width, height, tile, ctile),

@@ -234,3 +234,17 @@ def test_foveation_keeps_the_tile_set():
     b.decode([wv.ViewRequest(s, 0, 0.3, 0.1, 1.7, outs[1])])
     assert b.stats()["fine_tiles"] == t_fov
     assert b.sync_status() == 0
+
+
+def test_without_sharing_every_request_has_its_own_target():
+    from paper_2208_10859_gb300 import wv
+    st = _streams("yuv97", "ragged53")
+    reqs = _requests(st, 6, seed=9)
+    b = wv.Batch()
+    b.set_sharing(False)
+    b.decode(reqs)
+    torch.cuda.synchronize()
+    assert b.stats()["surfaces"] == len(reqs)
+    for r in reqs:
+        _assert_same(r, r.out.cpu().numpy())
+    assert b.sync_status() == 0
