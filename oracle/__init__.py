@@ -278,6 +278,7 @@ class Params:
     tlevels: int = 0           # inter-frame Haar levels k (set size n = 2^k)
     block: int = 256
     step: float = 1.0
+    stereo: int = 0            # 1: top/bottom stereo, each eye an equirect of height / 2
 
 
 def plane_dims(p: Params, plane: int) -> tuple[int, int]:
@@ -326,6 +327,8 @@ def _check_params(p: Params):
             raise ValueError("plane sides must be divisible by 2^levels")
     if p.wavelet == WAVELET_53 and (p.step != int(p.step) or p.step < 1):
         raise ValueError("5/3 needs an integer step >= 1")
+    if p.stereo not in (0, 1) or (p.stereo and p.height % (2 * CELL)):
+        raise ValueError("stereo frames need a height divisible by 64")
 
 
 def encode(frames, p: Params) -> bytes:
@@ -371,7 +374,7 @@ def encode(frames, p: Params) -> bytes:
     payload_off = table_off + table.nbytes
     payload_off = (payload_off + 255) // 256 * 256
     hdr = struct.pack(HEADER_FMT, MAGIC, 1, p.width, p.height, p.planes, p.chroma_420,
-                      p.levels, p.wavelet, p.num_frames, p.tlevels, p.block, 0, 0,
+                      p.levels, p.wavelet, p.num_frames, p.tlevels, p.block, 0, p.stereo,
                       float(p.step), nbpf, 0, len(payload), table_off, payload_off)
     out = bytearray(payload_off + len(payload) * B * B * 2)
     out[:len(hdr)] = hdr
@@ -389,10 +392,10 @@ class Stream:
             raise ValueError("truncated header")
         f = struct.unpack_from(HEADER_FMT, data, 0)
         (magic, version, w, h, planes, c420, levels, wavelet, nf, tl, blk, quant,
-         _r0, step, nbpf, _r1, npay, toff, poff) = f
-        if magic != MAGIC or version != 1 or quant != 0:
-            raise ValueError("bad magic/version/quantiser")
-        self.p = Params(w, h, planes, c420, levels, wavelet, nf, tl, blk, step)
+         stereo, step, nbpf, _r1, npay, toff, poff) = f
+        if magic != MAGIC or version != 1 or quant != 0 or stereo not in (0, 1):
+            raise ValueError("bad magic/version/quantiser/stereo flag")
+        self.p = Params(w, h, planes, c420, levels, wavelet, nf, tl, blk, step, stereo)
         _check_params(self.p)
         self.blocks = block_list(self.p)
         if nbpf != len(self.blocks):
@@ -478,11 +481,13 @@ def rotation(yaw: float, pitch: float) -> np.ndarray:
 
 
 def project(out_w: int, out_h: int, yaw: float, pitch: float, fov: float,
-            eq_w: int, eq_h: int):
+            eq_w: int, eq_h: int, row0: int = 0):
     """Equirectangular position (u, v), in pixels of an eq_w x eq_h frame with
     pixel centres at integers, seen by each viewport pixel (fp64).  The
     viewport is a pinhole camera with the same full field of view `fov` on
-    both axes; pixel (i, j) looks through its centre (i + 1/2, j + 1/2)."""
+    both axes; pixel (i, j) looks through its centre (i + 1/2, j + 1/2).
+    row0 places the equirect at rows row0 .. row0 + eq_h - 1 of a larger
+    frame (an eye of a top/bottom stereo frame)."""
     t = math.tan(fov / 2)
     xn = (2 * (np.arange(out_w) + 0.5) / out_w - 1) * t
     yn = (1 - 2 * (np.arange(out_h) + 0.5) / out_h) * t
@@ -492,8 +497,20 @@ def project(out_w: int, out_h: int, yaw: float, pitch: float, fov: float,
     lon = np.arctan2(d[..., 0], d[..., 2])
     lat = np.arctan2(d[..., 1], np.hypot(d[..., 0], d[..., 2]))
     u = (lon / (2 * math.pi) + 0.5) * eq_w - 0.5
-    v = (0.5 - lat / math.pi) * eq_h - 0.5
+    v = (0.5 - lat / math.pi) * eq_h - 0.5 + row0
     return u, v
+
+
+def eye_rows(p: Params, eye: int = 0) -> tuple[int, int]:
+    """(first row, rows) of the luma equirect an eye sees: the whole frame for
+    mono streams; the top (eye 0) or bottom (eye 1) half for stereo ones."""
+    if not p.stereo:
+        if eye != 0:
+            raise ValueError("mono streams have one eye")
+        return 0, p.height
+    if eye not in (0, 1):
+        raise ValueError("eye must be 0 or 1")
+    return eye * p.height // 2, p.height // 2
 
 
 def _fixed(t):
@@ -507,22 +524,24 @@ def _fixed(t):
     return i, f
 
 
-def taps(u, v, w: int, h: int):
-    """Integer positions of the 2x2 bilinear taps (x wraps, y clamps)."""
+def taps(u, v, w: int, h: int, rows=None):
+    """Integer positions of the 2x2 bilinear taps (x wraps, y clamps to the
+    rows (first, count) of the image, default all)."""
+    lo, n = (0, h) if rows is None else rows
     x0, fx = _fixed(np.asarray(u))
     y0, fy = _fixed(np.asarray(v))
     xa = np.mod(x0, w)
     xb = np.mod(x0 + 1, w)
-    ya = np.clip(y0, 0, h - 1)
-    yb = np.clip(y0 + 1, 0, h - 1)
+    ya = np.clip(y0, lo, lo + n - 1)
+    yb = np.clip(y0 + 1, lo, lo + n - 1)
     return xa, xb, ya, yb, fx, fy
 
 
-def bilinear(img: np.ndarray, u, v) -> np.ndarray:
+def bilinear(img: np.ndarray, u, v, rows=None) -> np.ndarray:
     """Fixed-point bilinear sample: weights in 1/256 steps that sum to 65536,
-    result (sum + 32768) >> 16."""
+    result (sum + 32768) >> 16; rows limits the clamp (stereo eyes)."""
     h, w = img.shape
-    xa, xb, ya, yb, fx, fy = taps(u, v, w, h)
+    xa, xb, ya, yb, fx, fy = taps(u, v, w, h, rows)
     P = img.astype(np.int64)
     acc = ((256 - fx) * (256 - fy) * P[ya, xa] + fx * (256 - fy) * P[ya, xb]
            + (256 - fx) * fy * P[yb, xa] + fx * fy * P[yb, xb])
@@ -538,7 +557,7 @@ CELL = 32  # luma pixels per mask cell: 256x256 cells for 8192x8192 (Sec. 3.1)
 
 
 def footprint(p: Params, out_w: int, out_h: int, yaw: float, pitch: float,
-              fov: float, cell: int = CELL):
+              fov: float, cell: int = CELL, eye: int = 0):
     """Low-resolution binary mask of the frame region the viewport reads
     (Sec. 3.1): cell (r, c) is set when a bilinear tap of some viewport pixel,
     of luma or (mapped to luma) of chroma, falls in it.  Returns (core,
@@ -546,16 +565,17 @@ def footprint(p: Params, out_w: int, out_h: int, yaw: float, pitch: float,
     in each direction (x wraps, y clamps)."""
     W, H = p.width, p.height
     rows, cols = H // cell, W // cell
-    u, v = project(out_w, out_h, yaw, pitch, fov, W, H)
+    r0, nr = eye_rows(p, eye)
+    u, v = project(out_w, out_h, yaw, pitch, fov, W, nr, r0)
     core = np.zeros((rows, cols), bool)
-    xa, xb, ya, yb, _, _ = taps(u, v, W, H)
+    xa, xb, ya, yb, _, _ = taps(u, v, W, H, (r0, nr))
     for xx in (xa, xb):
         for yy in (ya, yb):
             core[yy // cell, xx // cell] = True
     if p.planes == 3 and p.chroma_420:
         uc, vc = chroma_coords(u, v)
         cw, chh = W // 2, H // 2
-        xa, xb, ya, yb, _, _ = taps(uc, vc, cw, chh)
+        xa, xb, ya, yb, _, _ = taps(uc, vc, cw, chh, (r0 // 2, nr // 2))
         half = cell // 2
         for xx in (xa, xb):
             for yy in (ya, yb):
@@ -667,7 +687,7 @@ def cone_bytes(st: Stream, frame: int, mask: np.ndarray, keep=None) -> int:
 
 
 def fovea_distance(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: float,
-                   cell: int = CELL) -> np.ndarray:
+                   cell: int = CELL, eye: int = 0) -> np.ndarray:
     """Per mask cell (rows x cols), the angular distance (radians) of the
     cell centre from the gaze direction: max(|theta_x - gaze_x|,
     |theta_y - gaze_y|), theta_x = atan2(x, z) and theta_y = atan2(y, z) in
@@ -675,22 +695,24 @@ def fovea_distance(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: f
     view centre).  Cells behind the viewer (z <= 0) are infinitely far."""
     W, H = p.width, p.height
     rows, cols = H // cell, W // cell
+    r0, nr = eye_rows(p, eye)              # cells of the other eye are infinitely far
     lon = 2 * math.pi * ((np.arange(cols) + 0.5) * cell / W - 0.5)
-    lat = math.pi * (0.5 - (np.arange(rows) + 0.5) * cell / H)
+    lat = math.pi * (0.5 - ((np.arange(rows) + 0.5) * cell - r0) / nr)
     LON, LAT = np.meshgrid(lon, lat)
     d = np.stack([np.cos(LAT) * np.sin(LON), np.sin(LAT), np.cos(LAT) * np.cos(LON)], axis=-1)
     cam = d @ rotation(yaw, pitch)          # rows of R^T d: world -> viewer
     tx = np.arctan2(cam[..., 0], cam[..., 2])
     ty = np.arctan2(cam[..., 1], cam[..., 2])
     dist = np.maximum(np.abs(tx - gaze_x), np.abs(ty - gaze_y))
-    return np.where(cam[..., 2] > 0, dist, np.inf)
+    inside = ((np.arange(rows) * cell >= r0) & (np.arange(rows) * cell < r0 + nr))[:, None]
+    return np.where((cam[..., 2] > 0) & inside, dist, np.inf)
 
 
 def fovea_keep(p: Params, yaw: float, pitch: float, gaze_x: float, gaze_y: float,
-               r1: float, r2: float) -> dict:
+               r1: float, r2: float, eye: int = 0) -> dict:
     """Cell masks of the detail levels foveation keeps: {1: dist <= r1,
     2: dist <= r2}; other levels are complete."""
-    d = fovea_distance(p, yaw, pitch, gaze_x, gaze_y)
+    d = fovea_distance(p, yaw, pitch, gaze_x, gaze_y, eye=eye)
     return {1: d <= r1, 2: d <= r2}
 
 
@@ -745,30 +767,35 @@ def ycbcr_to_rgba(Y, Cb, Cr) -> np.ndarray:
     return np.stack([r, g, b, a], axis=-1).astype(np.uint8)
 
 
-def resample(planes, p: Params, u, v) -> np.ndarray:
-    """Viewport RGBA from decoded 8-bit planes at luma positions (u, v)."""
-    Y = bilinear(planes[0], u, v)
+def resample(planes, p: Params, u, v, eye: int = 0) -> np.ndarray:
+    """Viewport RGBA from decoded 8-bit planes at luma positions (u, v);
+    rows clamp to the eye's part of the frame."""
+    r0, nr = eye_rows(p, eye)
+    Y = bilinear(planes[0], u, v, (r0, nr))
     if p.planes == 1:
         return ycbcr_to_rgba(Y, np.full_like(Y, 128), np.full_like(Y, 128))
     if p.chroma_420:
         uc, vc = chroma_coords(u, v)
+        crows = (r0 // 2, nr // 2)
     else:
         uc, vc = u, v
-    return ycbcr_to_rgba(Y, bilinear(planes[1], uc, vc), bilinear(planes[2], uc, vc))
+        crows = (r0, nr)
+    return ycbcr_to_rgba(Y, bilinear(planes[1], uc, vc, crows), bilinear(planes[2], uc, vc, crows))
 
 
 def viewport(st: Stream, frame: int, yaw: float, pitch: float, fov: float,
-             out_w: int, out_h: int, planes=None, fovea=None) -> np.ndarray:
+             out_w: int, out_h: int, planes=None, fovea=None, eye: int = 0) -> np.ndarray:
     """Reference viewport decode by the plain definition: reconstruct the
     whole frame, then reproject it into the viewport.  fovea = (gaze_x,
-    gaze_y, r1, r2) decodes with foveation (Sec. 3.7).  Returns RGBA uint8
-    (out_h, out_w, 4)."""
+    gaze_y, r1, r2) decodes with foveation (Sec. 3.7); eye selects the half of
+    a top/bottom stereo frame.  Returns RGBA uint8 (out_h, out_w, 4)."""
     p = st.p
     if planes is None:
         keep = None if fovea is None else fovea_keep(p, yaw, pitch, *fovea)
         planes = [decode_plane(st, frame, pl, keep)[1] for pl in range(p.planes)]
-    u, v = project(out_w, out_h, yaw, pitch, fov, p.width, p.height)
-    return resample(planes, p, u, v)
+    r0, nr = eye_rows(p, eye)
+    u, v = project(out_w, out_h, yaw, pitch, fov, p.width, nr, r0)
+    return resample(planes, p, u, v, eye)
 
 
 def viewport_candidates(planes, p: Params, u, v, eps: float):

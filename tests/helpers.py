@@ -69,6 +69,20 @@ CASES["flat97"] = (lambda: [(np.full((128, 128), 77, np.uint8),)] * 2,
                    O.Params(128, 128, 1, 0, 3, O.WAVELET_97, 2, 1, 32, 4.0))
 
 
+# top/bottom stereo: a 256-wide frame holding two 256 x 128 equirects
+def _stereo_frames(n, seed):
+    fr = synth.equirect_gop(256, n, seed=seed, n_discs=5)
+    out = []
+    for f in fr:
+        # top eye: the upper half of the drawing squeezed to 2:1, bottom eye: its lower half
+        out.append(tuple(np.ascontiguousarray(np.vstack([pl[::2], pl[1::2]])) for pl in f))
+    return out
+
+
+CASES["stereo97"] = (lambda: _stereo_frames(2, 71),
+                     O.Params(256, 256, 3, 1, 4, O.WAVELET_97, 2, 1, 64, 2.0, 1))
+
+
 @functools.lru_cache(maxsize=None)
 def case(name: str):
     """(frames, params, stream bytes, oracle Stream) of a named workload."""
@@ -106,7 +120,7 @@ def other_rounding(x: np.ndarray, eps: float = 2e-3) -> np.ndarray:
     return np.clip(np.where(near_half(x, eps), alt, r), 0, 255).astype(np.uint8)
 
 
-def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov):
+def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov, eye: int = 0):
     """Per-pixel bound (eps_u, eps_v) in pixels on the float32 position error
     of the device projection: direction components carry a few float32
     rounding errors (~4e-7 relative), atan2f adds at most 2 ulp, and the
@@ -121,7 +135,7 @@ def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov):
     norm = np.linalg.norm(d, axis=-1)
     coslat = np.hypot(d[..., 0], d[..., 2]) / norm
     ku = p.width / (2 * math.pi)
-    kv = p.height / math.pi
+    kv = O.eye_rows(p, eye)[1] / math.pi
     eps_u = ku * (1.5e-6 / np.maximum(coslat, 1e-9) + 5e-7) + p.width * 2.0 ** -23
     eps_v = np.full_like(eps_u, kv * 1.5e-6 + p.height * 2.0 ** -23)
     return eps_u, eps_v
@@ -136,20 +150,22 @@ def quanta(t: np.ndarray, eps, k: int = 4):
     return np.stack(qs, -1), (hi - lo + 1) > k
 
 
-def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v):
+def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v, eye: int = 0):
     """Candidate RGBA values (n, k*k*k*k, 4) for sampled pixels whose exact
     positions are (u, v) +- (eps_u, eps_v); also a flag for pixels that need
     more than k quanta per axis (excluded from the check)."""
     qu, fu = quanta(u, eps_u)
     qv, fv = quanta(v, eps_v)
     n, k = u.shape[0], qu.shape[1]
-    Yc = np.stack([O.bilinear(planes[0], qu[:, a], qv[:, b]) for a in range(k) for b in range(k)], -1)
+    r0, nr = O.eye_rows(p, eye)
+    Yc = np.stack([O.bilinear(planes[0], qu[:, a], qv[:, b], (r0, nr)) for a in range(k) for b in range(k)], -1)
     if p.planes == 3:
         uc, vc = O.chroma_coords(u, v)
         quc, fuc = quanta(uc, eps_u / 2)
         qvc, fvc = quanta(vc, eps_v / 2)
-        Cb = np.stack([O.bilinear(planes[1], quc[:, a], qvc[:, b]) for a in range(k) for b in range(k)], -1)
-        Cr = np.stack([O.bilinear(planes[2], quc[:, a], qvc[:, b]) for a in range(k) for b in range(k)], -1)
+        cr_ = (r0 // 2, nr // 2)
+        Cb = np.stack([O.bilinear(planes[1], quc[:, a], qvc[:, b], cr_) for a in range(k) for b in range(k)], -1)
+        Cr = np.stack([O.bilinear(planes[2], quc[:, a], qvc[:, b], cr_) for a in range(k) for b in range(k)], -1)
         flag = fu | fv | fuc | fvc
     else:
         Cb = np.full_like(Yc, 128)
@@ -162,7 +178,7 @@ def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v):
     return O.ycbcr_to_rgba(Yx, Cbx, Crx), flag
 
 
-def viewport_mismatches(ref, p: O.Params, got: np.ndarray, yaw, pitch, fov):
+def viewport_mismatches(ref, p: O.Params, got: np.ndarray, yaw, pitch, fov, eye: int = 0):
     """Compare a GPU viewport (h, w, 4) with the oracle planes `ref` (list of
     (x, u8)): a pixel passes when it equals the oracle's value at one of the
     1/256 positions within the float32 error bound of its fp64 position (for
@@ -170,14 +186,15 @@ def viewport_mismatches(ref, p: O.Params, got: np.ndarray, yaw, pitch, fov):
     excused) pixel counts; excused pixels need more than four quanta per axis."""
     oh, ow = got.shape[:2]
     planes = [u8 for (_, u8) in ref]
-    u, v = O.project(ow, oh, yaw, pitch, fov, p.width, p.height)
-    eu, ev = position_error_bound(p, ow, oh, yaw, pitch, fov)
+    r0, nr = O.eye_rows(p, eye)
+    u, v = O.project(ow, oh, yaw, pitch, fov, p.width, nr, r0)
+    eu, ev = position_error_bound(p, ow, oh, yaw, pitch, fov, eye)
     u, v, eu, ev = u.ravel(), v.ravel(), eu.ravel(), ev.ravel()
     g = got.reshape(-1, 4)
-    cand, flag = rgba_candidates(planes, p, u, v, eu, ev)
+    cand, flag = rgba_candidates(planes, p, u, v, eu, ev, eye)
     ok = np.any(np.all(cand == g[:, None, :], axis=-1), axis=-1)
     if p.wavelet == O.WAVELET_97:
         alt = [other_rounding(x) for (x, _) in ref]
-        cand2, _ = rgba_candidates(alt, p, u, v, eu, ev)
+        cand2, _ = rgba_candidates(alt, p, u, v, eu, ev, eye)
         ok |= np.any(np.all(cand2 == g[:, None, :], axis=-1), axis=-1)
     return int(np.sum(~ok & ~flag)), int(np.sum(flag))

@@ -3,6 +3,7 @@ conversion (CPU only)."""
 import math
 
 import numpy as np
+import pytest
 
 import oracle as O
 
@@ -118,3 +119,23 @@ def test_candidates_include_exact_result():
     exact = O.resample(planes, p, u, v)
     cand = O.viewport_candidates(planes, p, u, v, 1e-3)
     assert np.all(np.any(np.all(cand == exact[..., None, :], axis=-1), axis=-1))
+
+
+def test_stereo_eye_resamples_its_half_only():
+    """Eye 1 of a top/bottom stereo frame [A; B] reprojects B exactly as a mono
+    frame B; eye 0 reprojects A; taps never cross into the other half."""
+    rng = np.random.default_rng(12)
+    p_mono = O.Params(128, 64, 3, 1, 2, O.WAVELET_97, 1, 0, 32, 1.0)
+    p_st = O.Params(128, 128, 3, 1, 2, O.WAVELET_97, 1, 0, 32, 1.0, 1)
+    A = [rng.integers(0, 256, (64, 128), dtype=np.uint8)] + [rng.integers(0, 256, (32, 64), dtype=np.uint8)] * 2
+    B = [rng.integers(0, 256, (64, 128), dtype=np.uint8)] + [rng.integers(0, 256, (32, 64), dtype=np.uint8)] * 2
+    st = [np.vstack([a, b]) for a, b in zip(A, B)]
+    for yaw, pitch, fov in [(0.3, 1.2, 1.5), (-2.0, -1.4, 1.2), (1.0, 0.0, 2.0)]:
+        for eye, mono in ((0, A), (1, B)):
+            r0, nr = O.eye_rows(p_st, eye)
+            u, v = O.project(40, 30, yaw, pitch, fov, 128, nr, r0)
+            um, vm = O.project(40, 30, yaw, pitch, fov, 128, 64)
+            np.testing.assert_allclose(v - r0, vm, rtol=0, atol=1e-9)
+            np.testing.assert_array_equal(O.resample(st, p_st, u, v, eye), O.resample(mono, p_mono, um, vm))
+    with pytest.raises(ValueError):
+        O.eye_rows(p_mono, 1)
