@@ -76,6 +76,8 @@ typedef struct {
     int block;
     int quant;
     float step;
+    int stereo;        /* 1: top/bottom stereo frames, each eye an equirect of
+                          height / 2 (eye 0 the top half); height % 64 == 0 */
 } wv_stream_desc;
 
 /* An RGBA8 output image in device memory, owned by the caller.  Row r starts
@@ -143,6 +145,13 @@ const char *wv_strerror(int code);
 int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch,
                        float fov, const wv_image *out);
 
+/* wv_decode_viewport for one eye of a top/bottom stereo stream (eye 0: the
+ * top half of the frame, 1: the bottom half; each half is an equirect of
+ * height / 2 rows and the bilinear taps clamp to its rows).  Mono streams
+ * accept eye 0 only (WV_ERR_ARG otherwise). */
+int wv_decode_viewport_eye(wv_stream *s, int frame, int eye, float yaw, float pitch,
+                           float fov, const wv_image *out);
+
 /* One viewport request of a batch.  The fields after `out` select foveated
  * decoding (Sec. 3.7): with fovea = 1 the details of wavelet level 1 (the
  * finest) are decoded only in mask cells whose centre lies within r1 of the
@@ -163,6 +172,7 @@ typedef struct {
     int fovea;
     float gaze_x, gaze_y;
     float r1, r2;
+    int eye;           /* stereo streams: 0 top, 1 bottom; mono: 0 */
 } wv_request;
 
 /* Decode n viewport requests, possibly of different streams, sizes, fields
@@ -287,6 +297,7 @@ typedef struct {
     int fovea;
     float gaze_x, gaze_y;
     float r1, r2;
+    int eye;
 } wv_server_request;
 
 typedef struct {

@@ -70,6 +70,7 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
     d->block = (int)h->block;
     d->quant = (int)h->quant;
     d->step = h->step;
+    d->stereo = (int)h->reserved0;
     Geom g;
     if (build_geom(*d, &g) != WV_OK) return WV_ERR_FORMAT;
     if ((int)h->nbpf != g.nbpf) return WV_ERR_FORMAT;
@@ -188,9 +189,18 @@ namespace wv {
 // Steps 1-3 of a viewport decode: footprint, tile lists and the tile decode
 // of the region an out_w x out_h viewport reads (into the stream's
 // reconstruction planes).
-int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h) {
+int eye_view(const Geom &g, int eye, int *row0, int *rows) {
+    if (eye < 0 || eye > (g.stereo ? 1 : 0)) return WV_ERR_ARG;
+    *rows = g.stereo ? g.p[0].h / 2 : g.p[0].h;
+    *row0 = eye * *rows;
+    return WV_OK;
+}
+
+int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h, int eye) {
     const Geom &g = s->g;
-    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
+    int row0, rows;
+    if (eye_view(g, eye, &row0, &rows) != WV_OK) return WV_ERR_ARG;
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
     const Bands b = stream_bands(s, frame);
     const uint32_t gen = next_gen(s);
     prof_begin(s, kKFootprint);
@@ -207,15 +217,17 @@ int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, in
 namespace {
 
 int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
-                    const wv_image *out) {
+                    const wv_image *out, int eye = 0) {
     if (!s) return WV_ERR_ARG;
     if (frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
     if (!(fov > 0.f && fov < 3.14159f) || !isfinite(yaw) || !isfinite(pitch)) return WV_ERR_ARG;
     if (check_image(out) != WV_OK) return WV_ERR_ARG;
     const Geom &g = s->g;
-    const int rc = wv::decode_region(s, frame, yaw, pitch, fov, out->width, out->height);
+    int row0, rows;
+    if (eye_view(g, eye, &row0, &rows) != WV_OK) return WV_ERR_ARG;
+    const int rc = wv::decode_region(s, frame, yaw, pitch, fov, out->width, out->height, eye);
     if (rc != WV_OK) return rc;
-    const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, g.p[0].h);
+    const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, rows, row0);
     prof_begin(s, kKResample);
     launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
     prof_end(s);
@@ -345,6 +357,8 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     if (d.wavelet == WV_WAVELET_53 && (d.step != floorf(d.step) || d.step > 65536.f))
         return WV_ERR_ARG;
     if (d.width < 2 || d.height < 2 || d.width > 16384 || d.height > 16384) return WV_ERR_ARG;
+    if (d.stereo != 0 && d.stereo != 1) return WV_ERR_ARG;
+    if (d.stereo && d.height % (2 * kCell)) return WV_ERR_ARG;
     if (d.width % kCell || d.height % kCell) return WV_ERR_ARG;
     g->planes = d.planes;
     g->c420 = d.planes == 3 ? d.chroma_420 : 0;
@@ -357,6 +371,7 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     while ((1 << g->log2b) < d.block) ++g->log2b;
     g->step = d.step;
     g->quant = d.quant;
+    g->stereo = d.stereo;
     g->cells_x = d.width / kCell;
     g->cells_y = d.height / kCell;
     g->tile = tile;
@@ -433,7 +448,7 @@ Frustum make_frustum(const View &v) {
     return f;
 }
 
-View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h) {
+View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h, int row0) {
     const double cy = cos((double)yaw), sy = sin((double)yaw);
     const double cp = cos((double)pitch), sp = sin((double)pitch);
     // R = R_y(yaw) R_x(pitch); R_x: (x, y, z) -> (x, y cp + z sp, -y sp + z cp)
@@ -449,9 +464,11 @@ View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w
     v.ku = (float)(eq_w / (2.0 * pi));
     v.cu = (float)(0.5 * eq_w - 0.5);
     v.kv = (float)(-eq_h / pi);
-    v.cv = (float)(0.5 * eq_h - 0.5);
+    v.cv = (float)(0.5 * eq_h - 0.5 + row0);
     v.out_w = out_w;
     v.out_h = out_h;
+    v.row0 = row0;
+    v.rows = eq_h;
     return v;
 }
 
@@ -604,6 +621,11 @@ int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fo
     return decode_viewport(s, frame, yaw, pitch, fov, out);
 }
 
+int wv_decode_viewport_eye(wv_stream *s, int frame, int eye, float yaw, float pitch, float fov,
+                           const wv_image *out) {
+    return decode_viewport(s, frame, yaw, pitch, fov, out, eye);
+}
+
 int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float) {
     if (!s || frame < 0 || frame >= s->g.num_frames || plane < 0 || plane >= s->g.planes)
         return WV_ERR_ARG;
@@ -635,7 +657,9 @@ int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_
                        uint8_t *mask_host, int *tiles) {
     if (!s || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f)) return WV_ERR_ARG;
     const Geom &g = s->g;
-    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, g.p[0].h);
+    int row0, rows;
+    eye_view(g, 0, &row0, &rows);
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
     uint8_t *m = s->mask;
     const uint32_t gen = next_gen(s);
     launch_footprint(g, v, m, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
@@ -654,7 +678,9 @@ int wv_debug_project(wv_stream *s, float yaw, float pitch, float fov, int out_w,
                      float *uv_dev) {
     if (!s || !uv_dev || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f))
         return WV_ERR_ARG;
-    const View v = make_view(yaw, pitch, fov, out_w, out_h, s->g.p[0].w, s->g.p[0].h);
+    int row0, rows;
+    eye_view(s->g, 0, &row0, &rows);
+    const View v = make_view(yaw, pitch, fov, out_w, out_h, s->g.p[0].w, rows, row0);
     launch_project(v, uv_dev, s->cs);
     return cuda_err(cudaGetLastError());
 }

@@ -100,6 +100,8 @@ int check_request(const wv_request &r) {
         (o->pitch_bytes % 4) != 0 || ((uintptr_t)o->dptr % 4) != 0)
         return WV_ERR_ARG;
     if (r.fovea != 0 && r.fovea != 1) return WV_ERR_ARG;
+    int row0, rows;
+    if (eye_view(r.s->g, r.eye, &row0, &rows) != WV_OK) return WV_ERR_ARG;
     if (r.fovea && (!isfinite(r.gaze_x) || !isfinite(r.gaze_y) || isnan(r.r1) || isnan(r.r2)))
         return WV_ERR_ARG;
     return WV_OK;
@@ -252,7 +254,9 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         const Surface &S = P.surf[P.req_surface[i]];
         RequestJob R;
         memset(&R, 0, sizeof(R));
-        R.v = make_view(r.yaw, r.pitch, r.fov, r.out.width, r.out.height, S.g.p[0].w, S.g.p[0].h);
+        int row0, rows;
+        eye_view(S.g, r.eye, &row0, &rows);   // validated by check_request
+        R.v = make_view(r.yaw, r.pitch, r.fov, r.out.width, r.out.height, S.g.p[0].w, rows, row0);
         R.f = make_frustum(R.v);
         R.fov.on = r.fovea;
         R.fov.gx = r.gaze_x;

@@ -323,6 +323,7 @@ int run(const Geom &g, const void *const *planes, char *base, const ScratchLayou
     h.tlevels = g.tlevels;
     h.block = g.block;
     h.quant = 0;
+    h.reserved0 = (uint32_t)g.stereo;
     h.step = g.step;
     h.nbpf = g.nbpf;
     h.n_payload = nslots;

@@ -127,6 +127,15 @@ __device__ __forceinline__ uint8_t fovea_bits(const View &v, const Fovea &fv, in
     return (uint8_t)((d <= fv.r1 ? 1 : 0) | (d <= fv.r2 ? 2 : 0));
 }
 
+// Whether cell (cx, cy) of the frame is needed by the eye's equirect (rows
+// v.row0 .. v.row0 + v.rows - 1; cells of the other eye of a stereo frame
+// never are).
+__device__ __forceinline__ bool cell_needed_eye(const View &v, const Frustum &f, int eq_w, int cx, int cy) {
+    const int c0 = v.row0 >> kLogCell, nc = v.rows >> kLogCell;
+    if (cy < c0 || cy >= c0 + nc) return false;
+    return cell_needed(f, eq_w, v.rows, nc, cx, cy - c0);
+}
+
 __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mask,
                             uint32_t *__restrict__ tile_gen, uint32_t *__restrict__ ctile_gen,
                             uint32_t gen, int *counters) {
@@ -134,7 +143,7 @@ __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mas
     const int cy = blockIdx.y * blockDim.y + threadIdx.y;
     if (cx == 0 && cy == 0) counters[0] = counters[1] = 0;   // tile counts of this viewport
     if (cx >= g.cells_x || cy >= g.cells_y) return;
-    const bool hit = cell_needed(f, g.p[0].w, g.p[0].h, g.cells_y, cx, cy);
+    const bool hit = cell_needed_eye(v, f, g.p[0].w, cx, cy);
     mask[cy * g.cells_x + cx] = hit ? 1 : 0;
     if (hit) stamp_cell(g, cx, cy, tile_gen, ctile_gen, gen);
 }
@@ -149,10 +158,13 @@ __global__ void k_footprint_batch(const RequestJob *__restrict__ reqs,
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
     const int cy = blockIdx.y * blockDim.y + threadIdx.y;
     if (cx >= g.cells_x || cy >= g.cells_y) return;
-    if (cell_needed(r.f, g.p[0].w, g.p[0].h, g.cells_y, cx, cy))
+    if (cell_needed_eye(r.v, r.f, g.p[0].w, cx, cy))
         stamp_cell(g, cx, cy, s.stamp, s.stamp + g.total_tiles, 1u);
-    if (r.fov.on && s.fmask)
-        s.fmask[cy * g.cells_x + cx] = fovea_bits(r.v, r.fov, g.p[0].w, g.p[0].h, cx, cy);
+    if (r.fov.on && s.fmask) {
+        const int c0 = r.v.row0 >> kLogCell, nc = r.v.rows >> kLogCell;
+        s.fmask[cy * g.cells_x + cx] =
+            (cy >= c0 && cy < c0 + nc) ? fovea_bits(r.v, r.fov, g.p[0].w, r.v.rows, cx, cy - c0) : 0;
+    }
 }
 
 // Tile entry: plane << 28 | ty << 14 | tx, from index t of the plane-ordered

@@ -75,6 +75,7 @@ int paper_parse(const void *bytes, size_t n, wv_stream_desc *d, PaperInfo *info)
     d->block = 32;
     d->quant = 1;
     d->step = 1.f;
+    d->stereo = 0;
     Geom g;
     if (build_geom(*d, &g) != WV_OK || (int)h.nbpf != g.nbpf) return WV_ERR_FORMAT;
     const char *base = (const char *)bytes;

@@ -907,7 +907,9 @@ int wv_decode_viewport_filtered(wv_stream *s, int frame, float yaw, float pitch,
     // the region decode of the plain path, then the planes instead of RGBA
     int rc = wv::decode_region(s, frame, yaw, pitch, fov, out->width, out->height);
     if (rc != WV_OK) return rc;
-    const View v = make_view(yaw, pitch, fov, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
+    int row0, rows;
+    eye_view(s->g, 0, &row0, &rows);   // eye 0 (the top half of a stereo frame)
+    const View v = make_view(yaw, pitch, fov, out->width, out->height, s->g.p[0].w, rows, row0);
     launch_resample(s->g, v, s->recon, nullptr, nullptr, 0, s->cs, c->xbuf, c->cb, c->cr);
     ConvArgs fin;
     memset(&fin, 0, sizeof(fin));

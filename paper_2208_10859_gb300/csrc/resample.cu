@@ -28,7 +28,7 @@ struct Taps {
     int fx, fy;
 };
 
-__device__ __forceinline__ Taps bilinear_taps(int w, int h, float u, float v) {
+__device__ __forceinline__ Taps bilinear_taps(int w, int r_lo, int r_n, float u, float v) {
     int x0, fx, y0, fy;
     fixed_split(u, x0, fx);
     fixed_split(v, y0, fy);
@@ -40,8 +40,8 @@ __device__ __forceinline__ Taps bilinear_taps(int w, int h, float u, float v) {
         if (xa < 0) xa += w;
     }
     const int xb = (xa + 1 == w) ? 0 : xa + 1;
-    const int ya = min(max(y0, 0), h - 1) * w;
-    const int yb = min(max(y0 + 1, 0), h - 1) * w;
+    const int ya = min(max(y0, r_lo), r_lo + r_n - 1) * w;
+    const int yb = min(max(y0 + 1, r_lo), r_lo + r_n - 1) * w;
     Taps t;
     t.a0 = ya + xa;
     t.a1 = ya + xb;
@@ -60,10 +60,11 @@ __device__ __forceinline__ int blend(const uint8_t *__restrict__ img, const Taps
     return ((256 - t.fy) * top + t.fy * bot + 32768) >> 16;
 }
 
-// Y, Cb, Cr of luma position (u, v); Cb and Cr share their taps.
+// Y, Cb, Cr of luma position (u, v); Cb and Cr share their taps.  Rows
+// clamp to the eye's part of the frame (all of it for mono streams).
 __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, float v, int &y, int &cb,
                                              int &cr) {
-    y = blend(a.plane[0], bilinear_taps(a.w[0], a.h[0], u, v));
+    y = blend(a.plane[0], bilinear_taps(a.w[0], a.v.row0, a.v.rows, u, v));
     cb = cr = 128;
     if (a.planes == 3) {
         float uc = u, vc = v;
@@ -71,7 +72,8 @@ __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, flo
             uc = fmaf(u + 0.5f, 0.5f, -0.5f);
             vc = fmaf(v + 0.5f, 0.5f, -0.5f);
         }
-        const Taps t = bilinear_taps(a.w[1], a.h[1], uc, vc);
+        const int sh = a.c420 ? 1 : 0;
+        const Taps t = bilinear_taps(a.w[1], a.v.row0 >> sh, a.v.rows >> sh, uc, vc);
         cb = blend(a.plane[1], t);
         cr = blend(a.plane[2], t);
     }

@@ -177,6 +177,7 @@ wv_request to_request(const SvReq &q, wv_stream *s) {
     r.gaze_y = q.r.gaze_y;
     r.r1 = q.r.r1;
     r.r2 = q.r.r2;
+    r.eye = q.r.eye;
     return r;
 }
 

@@ -48,6 +48,7 @@ struct PlaneGeom {
 struct Geom {
     int planes, c420, levels, wavelet, num_frames, tlevels, block, log2b, nbpf;
     int quant;   // 0: dead-zone uniform quantiser (step); 1: byte quantiser of the paper format
+    int stereo;  // 1: top/bottom stereo frames
     float step;
     PlaneGeom p[3];
     int cells_x, cells_y;
@@ -77,6 +78,7 @@ struct View {
     float t, sx, sy;
     float ku, cu, kv, cv;
     int out_w, out_h;
+    int row0, rows;   // luma rows of the equirect the eye sees (stereo: half the frame)
 };
 
 // Inward unit normals (world coordinates) of the viewport frustum's four
@@ -205,10 +207,12 @@ cudaError_t paper_transcode(const void *bytes, size_t n, const PaperInfo &info, 
                             cudaStream_t cs);
 
 // host helpers (api.cu)
-int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h);
+int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h,
+                  int eye = 0);
 int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
 Bands frame_bands(const Geom &g, int frame);
-View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h);
+View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h, int row0 = 0);
+int eye_view(const Geom &g, int eye, int *row0, int *rows);   // WV_ERR_ARG for an invalid eye
 Frustum make_frustum(const View &v);
 
 // kernel launchers

@@ -32,7 +32,7 @@ class StreamDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("planes", ctypes.c_int),
                 ("chroma_420", ctypes.c_int), ("levels", ctypes.c_int), ("wavelet", ctypes.c_int),
                 ("num_frames", ctypes.c_int), ("tlevels", ctypes.c_int), ("block", ctypes.c_int),
-                ("quant", ctypes.c_int), ("step", ctypes.c_float)]
+                ("quant", ctypes.c_int), ("step", ctypes.c_float), ("stereo", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -47,7 +47,7 @@ class Request(ctypes.Structure):
     _fields_ = [("s", ctypes.c_void_p), ("frame", ctypes.c_int), ("yaw", ctypes.c_float),
                 ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image),
                 ("fovea", ctypes.c_int), ("gaze_x", ctypes.c_float), ("gaze_y", ctypes.c_float),
-                ("r1", ctypes.c_float), ("r2", ctypes.c_float)]
+                ("r1", ctypes.c_float), ("r2", ctypes.c_float), ("eye", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -64,7 +64,7 @@ class ServerRequest(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_int), ("frame", ctypes.c_int), ("yaw", ctypes.c_float),
                 ("pitch", ctypes.c_float), ("fov", ctypes.c_float), ("out", Image),
                 ("fovea", ctypes.c_int), ("gaze_x", ctypes.c_float), ("gaze_y", ctypes.c_float),
-                ("r1", ctypes.c_float), ("r2", ctypes.c_float)]
+                ("r1", ctypes.c_float), ("r2", ctypes.c_float), ("eye", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -101,6 +101,7 @@ def _lib():
             "wv_set_cuda_stream": (c_int, [vp, vp]),
             "wv_close_stream": (None, [vp]),
             "wv_decode_viewport": (c_int, [vp, c_int, fl, fl, fl, ctypes.POINTER(Image)]),
+            "wv_decode_viewport_eye": (c_int, [vp, c_int, c_int, fl, fl, fl, ctypes.POINTER(Image)]),
             "wv_decode_batch": (c_int, [ctypes.POINTER(Request), c_int, vp]),
             "wv_decode_full": (c_int, [vp, c_int, c_int, vp, c_int]),
             "wv_stream_sync_status": (c_int, [vp]),
@@ -169,7 +170,8 @@ def exported_symbols() -> list[str]:
     """Names of the ABI functions the binding resolves (all of include/wv.h)."""
     _lib()
     return ["wv_strerror", "wv_stream_query", "wv_open_stream", "wv_set_cuda_stream",
-            "wv_close_stream", "wv_decode_viewport", "wv_decode_batch", "wv_decode_full",
+            "wv_close_stream", "wv_decode_viewport", "wv_decode_viewport_eye", "wv_decode_batch",
+            "wv_decode_full",
             "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
             "wv_set_decode_mode",
@@ -242,10 +244,14 @@ class Stream:
         _check(_lib().wv_set_cuda_stream(self._handle, ctypes.c_void_p(_cuda_stream_handle(stream))),
                "wv_set_cuda_stream")
 
-    def decode_viewport(self, frame: int, yaw: float, pitch: float, fov: float, out) -> None:
+    def decode_viewport(self, frame: int, yaw: float, pitch: float, fov: float, out, eye: int = 0) -> None:
         img = _image(out)
-        _check(_lib().wv_decode_viewport(self._handle, frame, yaw, pitch, fov, ctypes.byref(img)),
-               "wv_decode_viewport")
+        if eye == 0:
+            _check(_lib().wv_decode_viewport(self._handle, frame, yaw, pitch, fov, ctypes.byref(img)),
+                   "wv_decode_viewport")
+        else:
+            _check(_lib().wv_decode_viewport_eye(self._handle, frame, eye, yaw, pitch, fov, ctypes.byref(img)),
+                   "wv_decode_viewport_eye")
 
     def decode_full(self, frame: int, plane: int, out=None, as_float: bool = False) -> None:
         ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
@@ -337,13 +343,14 @@ class ViewRequest:
     gaze_y: float = 0.0
     r1: float = float("inf")
     r2: float = float("inf")
+    eye: int = 0
 
 
 def _requests(requests: list):
     arr = (Request * len(requests))()
     for i, r in enumerate(requests):
         arr[i] = Request(r.stream.handle, r.frame, r.yaw, r.pitch, r.fov, _image(r.out),
-                         1 if r.fovea else 0, r.gaze_x, r.gaze_y, r.r1, r.r2)
+                         1 if r.fovea else 0, r.gaze_x, r.gaze_y, r.r1, r.r2, r.eye)
     return arr
 
 
@@ -486,9 +493,9 @@ class Server:
 
     def submit(self, stream_id: int, frame: int, yaw: float, pitch: float, fov: float, out,
                fovea: bool = False, gaze_x: float = 0.0, gaze_y: float = 0.0,
-               r1: float = float("inf"), r2: float = float("inf")) -> int:
+               r1: float = float("inf"), r2: float = float("inf"), eye: int = 0) -> int:
         r = ServerRequest(stream_id, frame, yaw, pitch, fov, _image(out), 1 if fovea else 0,
-                          gaze_x, gaze_y, r1, r2)
+                          gaze_x, gaze_y, r1, r2, eye)
         t = ctypes.c_uint64()
         _check(_lib().wv_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "wv_server_submit")
         return t.value
