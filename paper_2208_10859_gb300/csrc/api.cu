@@ -590,6 +590,20 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     else if (e == cudaSuccess && h.n_payload)
         e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
                             h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
+    // 9/7 dead-zone codes become t = 2q + sign(q) on the device when every
+    // |q| <= kDzTMax (the tile decoder then needs no sign logic)
+    if (e == cudaSuccess && !is_paper && h.n_payload && s->g.wavelet == WV_WAVELET_97 && s->g.quant == 0) {
+        const size_t count = (size_t)h.n_payload * s->g.block * s->g.block;
+        int max_abs = 0;
+        e = cudaMemsetAsync(s->counters + 8, 0, 4, s->cs);
+        if (e == cudaSuccess) e = payload_max_abs(s->payload, count, s->counters + 8, s->cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&max_abs, s->counters + 8, 4, cudaMemcpyDeviceToHost, s->cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+        if (e == cudaSuccess && max_abs <= kDzTMax) {
+            e = payload_to_deadzone_t(s->payload, count, s->cs);
+            s->g.dz_t = 1;
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.tile_gen, 0, L.total - L.tile_gen, s->cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);

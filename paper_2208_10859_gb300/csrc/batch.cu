@@ -132,8 +132,10 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         const Geom &sg = r.s->g;
         const std::pair<int, int> ts = tile_shape(b, sg);
         if (build_geom(r.s->desc, &S.g, ts.first, ts.second) != WV_OK) return WV_ERR_ARG;
+        S.g.dz_t = sg.dz_t;   // the code form of the stream's device payload
         // 1 + tlevels coefficient frames
-        S.cls = 2 * kMaxBands * S.g.wavelet + kMaxBands * (S.foveated ? 1 : 0) + S.g.tlevels;
+        const int group = S.g.dz_t ? 4 + (S.foveated ? 1 : 0) : 2 * S.g.wavelet + (S.foveated ? 1 : 0);
+        S.cls = kMaxBands * group + S.g.tlevels;
         P.req_surface[i] = (int)P.surf.size();
         if (!r.fovea) shared[{r.s, r.frame}] = (int)P.surf.size();
         P.surf.push_back(S);
@@ -306,7 +308,9 @@ cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool tim
     if (timed) cudaEventRecord(b->ev[2], cs);
     for (int c = 0; c < kClasses; ++c) {
         if (!P.smem[c]) continue;
-        e = launch_decode_batch(c / (2 * kMaxBands), c % kMaxBands + 1, (c / kMaxBands) % 2 == 1, surfs,
+        const int group = c / kMaxBands;
+        e = launch_decode_batch(group >= 4 ? WV_WAVELET_97 : group / 2, c % kMaxBands + 1, group % 2 == 1,
+                                group >= 4, surfs,
                                 lists.coarse[c], lists.fine[c], ctr + 4 * c,
                                 ctr + kBatchCtr, (int *)(base + P.err), P.smem[c], cs);
         if (e != cudaSuccess) return e;

@@ -27,6 +27,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -118,6 +119,15 @@ __device__ __forceinline__ LevelGeo make_level(int l, Range ox, Range oy, int pw
 __device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xffffu); }
 __device__ __forceinline__ int hi16(uint32_t w) { return (int)(int16_t)(w >> 16); }
 
+// Both int16 halves of a word as floats, exactly and without a conversion
+// instruction: each half, biased to unsigned (v + 2^15), becomes the low
+// mantissa bits of 2^23, and 2^23 + 2^15 is subtracted.
+__device__ __forceinline__ void halves_to_float(uint32_t w, float &lo, float &hi) {
+    const uint32_t x = w ^ 0x80008000u;
+    lo = __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8421376.0f;
+    hi = __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8421376.0f;
+}
+
 template <int NB>
 struct Raw {
     uint4 q[2][NB];      // [even/odd columns][band]
@@ -125,6 +135,11 @@ struct Raw {
     int keep[2];         // foveation: bit 0 keeps coefficients 0-3, bit 1 keeps 4-7
 };
 
+// QM = 2: dead-zone codes stored as t = 2q + sign(q) (transcoded when the
+// stream was opened, |q| <= kDzTMax), so c = t step / 2 needs no sign logic;
+// with two bands the pair L +- H is formed as 16-bit integers (|t| <= 16383:
+// the sum fits) and converted once.  Results equal those of QM = 0 exactly:
+// every intermediate is an integer below 2^24.
 // QM = 1: the byte quantiser of the paper-faithful format (Sec. 3.3): a
 // stored value v > 0 is code + 1 and decodes to c_min + code (c_max - c_min)
 // / 255 of its coefficient frame, plane and class (cls 0: approximation
@@ -132,7 +147,38 @@ struct Raw {
 template <int WAV, int NB, int QM = 0>
 __device__ __forceinline__ void combine8(const TileArgs &a, const uint4 *q, const bool *have,
                                          float s, int plane, int cls, typename Traits<WAV>::T out[8]) {
-    if constexpr (WAV == 1 && QM == 1) {
+    if constexpr (WAV == 1 && QM == 2 && NB == 2) {
+        const bool add = a.bands.bit[1];
+        const uint32_t w0[4] = {q[0].x, q[0].y, q[0].z, q[0].w};
+        const uint32_t w1[4] = {q[1].x, q[1].y, q[1].z, q[1].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t l = have[0] ? w0[k] : 0u, h = have[1] ? w1[k] : 0u;
+            float lo, hi;
+            halves_to_float(add ? __vadd2(l, h) : __vsub2(l, h), lo, hi);
+            out[2 * k] = lo * s;
+            out[2 * k + 1] = hi * s;
+        }
+    } else if constexpr (WAV == 1 && QM == 2) {
+        float acc[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (!have[b] || (q[b].x | q[b].y | q[b].z | q[b].w) == 0) continue;
+            const uint32_t w[4] = {q[b].x, q[b].y, q[b].z, q[b].w};
+            const float sg = (b == 0 || a.bands.bit[b]) ? 1.f : -1.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float lo, hi;
+                halves_to_float(w[k], lo, hi);
+                acc[2 * k] = fmaf(sg, lo, acc[2 * k]);
+                acc[2 * k + 1] = fmaf(sg, hi, acc[2 * k + 1]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) out[m] = acc[m] * s;
+    } else if constexpr (WAV == 1 && QM == 1) {
         float acc[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[m] = 0.f;
@@ -452,14 +498,14 @@ __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &
         t.fast = fast_x;
         return t;
     };
-    for (int base = warp * rpw; base < G.rows; base += 2 * stride) {
-        const Task t0 = make(base + r_in);
-        const Task t1 = make(base + stride + r_in);
-        Raw<NB> r0, r1;
-        load_task<WAV, NB, FOV>(a, pg, G, t0, r0);
-        load_task<WAV, NB, FOV>(a, pg, G, t1, r1);
-        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t0, r0, P, nch, A);
-        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t1, r1, P, nch, A);
+    // one row task per lane and iteration: the coefficient loads are not
+    // what limits this loop (it is issue-bound), and a single task in flight
+    // leaves the registers to the scheduler
+    for (int base = warp * rpw; base < G.rows; base += stride) {
+        const Task t = make(base + r_in);
+        Raw<NB> r;
+        load_task<WAV, NB, FOV>(a, pg, G, t, r);
+        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t, r, P, nch, A);
     }
 }
 
@@ -773,7 +819,7 @@ __device__ __forceinline__ bool wait_at_least(const int *flag, int target) {
     return false;
 }
 
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, int QM>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tiles_batch(const SurfaceJob *__restrict__ surfs, const uint2 *__restrict__ coarse,
                   const uint2 *__restrict__ fine, int *cls, int *surf, int *err) {
@@ -808,7 +854,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             reinterpret_cast<int *>(&sa)[k] = __ldg(src + k);
         __syncthreads();
         float *P = smem + sa.a_floats;   // a_floats and p_floats fit the launch's shared memory
-        decode_one<WAV, NB, FOV>(sa, w.y, A, P);
+        decode_one<WAV, NB, FOV, QM>(sa, w.y, A, P);
         if (kind == 0) __threadfence();   // LL_2 stores visible GPU-wide before the count
         __syncthreads();
         if (kind == 0 && threadIdx.x == 0) atomicAdd(&surf[2 * (int)w.x + 1], 1);
@@ -899,24 +945,24 @@ cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) 
     return cudaGetLastError();
 }
 
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, int QM>
 cudaError_t launch_batch_t(const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
                            int *cls, int *surf, int *err, int smem_bytes, cudaStream_t cs) {
     static int opted[64] = {};
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || smem_bytes > opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles_batch<WAV, NB, FOV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tiles_batch<WAV, NB, FOV, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) opted[dev] = smem_bytes;
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_batch<WAV, NB, FOV>, kThreads,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_batch<WAV, NB, FOV, QM>, kThreads,
                                                                   smem_bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    k_tiles_batch<WAV, NB, FOV><<<sms * per_sm, kThreads, smem_bytes, cs>>>(surfs, coarse, fine, cls, surf, err);
+    k_tiles_batch<WAV, NB, FOV, QM><<<sms * per_sm, kThreads, smem_bytes, cs>>>(surfs, coarse, fine, cls, surf, err);
     return cudaGetLastError();
 }
 
@@ -934,6 +980,14 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
         case 2: return launch_t<1, 2, 1>(a, grid, threads, cs);
         case 3: return launch_t<1, 3, 1>(a, grid, threads, cs);
         default: return launch_t<1, 4, 1>(a, grid, threads, cs);
+        }
+    }
+    if (a.g.wavelet == WV_WAVELET_97 && a.g.dz_t) {   // codes stored as 2q + sign(q)
+        switch (nb) {
+        case 1: return launch_t<1, 1, 2>(a, grid, threads, cs);
+        case 2: return launch_t<1, 2, 2>(a, grid, threads, cs);
+        case 3: return launch_t<1, 3, 2>(a, grid, threads, cs);
+        default: return launch_t<1, 4, 2>(a, grid, threads, cs);
         }
     }
     if (a.g.wavelet == WV_WAVELET_97) {
@@ -1040,25 +1094,85 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
 
 // One persistent launch decoding every listed coarse and fine tile of a batch
 // (surfaces whose coefficient frames number nb).
-template <int WAV, bool FOV>
+template <int WAV, bool FOV, int QM>
 cudaError_t launch_batch_nb(int nb, const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
                             int *cls_ctr, int *surf_ctr, int *err, int smem_bytes, cudaStream_t cs) {
     switch (nb) {
-    case 1: return launch_batch_t<WAV, 1, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    case 2: return launch_batch_t<WAV, 2, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    case 3: return launch_batch_t<WAV, 3, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    default: return launch_batch_t<WAV, 4, FOV>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 1: return launch_batch_t<WAV, 1, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 2: return launch_batch_t<WAV, 2, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 3: return launch_batch_t<WAV, 3, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    default: return launch_batch_t<WAV, 4, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
     }
 }
 
-cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, const SurfaceJob *surfs,
+cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
                                 const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
                                 int *err, int smem_bytes, cudaStream_t cs) {
+    if (wavelet == WV_WAVELET_97 && dz_t)
+        return fovea ? launch_batch_nb<1, true, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
+                     : launch_batch_nb<1, false, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
     if (wavelet == WV_WAVELET_97)
-        return fovea ? launch_batch_nb<1, true>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
-                     : launch_batch_nb<1, false>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    return fovea ? launch_batch_nb<0, true>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
-                 : launch_batch_nb<0, false>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+        return fovea ? launch_batch_nb<1, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
+                     : launch_batch_nb<1, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    return fovea ? launch_batch_nb<0, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
+                 : launch_batch_nb<0, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+}
+
+// ---- dead-zone codes as 2q + sign(q) -----------------------------------------
+
+namespace {
+
+__global__ void k_payload_max_abs(const int4 *__restrict__ p, size_t n, int *out) {
+    int m = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int4 v = __ldcs(p + i);
+        const uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m = max(m, max(abs(lo16(w[k])), abs(hi16(w[k]))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__device__ __forceinline__ uint32_t to_t(uint32_t w) {
+    const int lo = lo16(w), hi = hi16(w);
+    const int tl = 2 * lo + min(max(lo, -1), 1), th = 2 * hi + min(max(hi, -1), 1);
+    return ((uint32_t)tl & 0xffffu) | ((uint32_t)th << 16);
+}
+
+__global__ void k_payload_to_t(int4 *__restrict__ p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        int4 v = p[i];
+        v.x = (int)to_t((uint32_t)v.x);
+        v.y = (int)to_t((uint32_t)v.y);
+        v.z = (int)to_t((uint32_t)v.z);
+        v.w = (int)to_t((uint32_t)v.w);
+        p[i] = v;
+    }
+}
+
+int grid_for(size_t n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int)std::min<size_t>((n + 255) / 256, (size_t)sms * 8);
+}
+
+}  // namespace
+
+cudaError_t payload_max_abs(const int16_t *payload, size_t count, int *dev_word, cudaStream_t cs) {
+    const size_t n = count / 8;   // block payloads are multiples of 256 codes
+    if (n == 0) return cudaSuccess;
+    k_payload_max_abs<<<grid_for(n), 256, 0, cs>>>(reinterpret_cast<const int4 *>(payload), n, dev_word);
+    return cudaGetLastError();
+}
+
+cudaError_t payload_to_deadzone_t(int16_t *payload, size_t count, cudaStream_t cs) {
+    const size_t n = count / 8;
+    if (n == 0) return cudaSuccess;
+    k_payload_to_t<<<grid_for(n), 256, 0, cs>>>(reinterpret_cast<int4 *>(payload), n);
+    return cudaGetLastError();
 }
 
 }  // namespace wv

@@ -49,6 +49,7 @@ struct Geom {
     int planes, c420, levels, wavelet, num_frames, tlevels, block, log2b, nbpf;
     int quant;   // 0: dead-zone uniform quantiser (step); 1: byte quantiser of the paper format
     int stereo;  // 1: top/bottom stereo frames
+    int dz_t;    // 9/7 dead zone: the device payload holds t = 2q + sign(q) (set at open)
     float step;
     PlaneGeom p[3];
     int cells_x, cells_y;
@@ -160,9 +161,11 @@ struct SurfaceJob {
 };
 
 // Decode classes of a batch: one persistent tile-decode launch per wavelet,
-// foveation (a separately compiled kernel) and number of coefficient frames
-// present: class = 2 kMaxBands wavelet + kMaxBands foveated + frames - 1.
-constexpr int kClasses = 4 * kMaxBands;
+// foveation (a separately compiled kernel), code form and number of
+// coefficient frames present: class = kMaxBands group + frames - 1 with
+// group = 2 wavelet + foveated for codes q, 4 + foveated for 9/7 codes held
+// as 2q + sign(q).
+constexpr int kClasses = 6 * kMaxBands;
 
 // Work lists of a batch, one pair per decode class.
 struct BatchLists {
@@ -249,7 +252,12 @@ void launch_footprint_batch(const RequestJob *reqs, const SurfaceJob *surfs, int
                             int max_cy, cudaStream_t cs);
 void launch_select_batch(const SurfaceJob *surfs, int m, int max_stamps, const BatchLists &lists,
                          int *ctr, cudaStream_t cs);
-cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, const SurfaceJob *surfs,
+// Largest |q| for which an opened 9/7 dead-zone stream keeps its codes as
+// t = 2q + sign(q) on the device (|t| <= 16383: two bands add in 16 bits).
+constexpr int kDzTMax = 8191;
+cudaError_t payload_max_abs(const int16_t *payload, size_t count, int *dev_word, cudaStream_t cs);
+cudaError_t payload_to_deadzone_t(int16_t *payload, size_t count, cudaStream_t cs);
+cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
                                 const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
                                 int *err, int smem_bytes, cudaStream_t cs);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
