@@ -89,7 +89,8 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
 }
 
 struct Layout {
-    size_t payload, table, recon[3], ll2[3], mask, tiles, ctiles, tile_gen, ctile_gen, counters, err, total;
+    size_t payload, table, recon[3], ll2[3], mask, tiles, ctiles, tile_gen, ctile_gen, counters, err;
+    size_t ll2_1[3], tiles1, ctiles1, counters1, total;   // the second per-viewport set
 };
 
 Layout layout(const Geom &g, uint64_t n_payload) {
@@ -121,6 +122,17 @@ Layout layout(const Geom &g, uint64_t n_payload) {
     L.counters = o;
     o = align256(o + 64);
     L.err = o;
+    o = align256(o + 64);
+    for (int p = 0; p < 3; ++p) {
+        L.ll2_1[p] = o;
+        if (p < g.planes && g.levels >= 3)
+            o = align256(o + (size_t)g.p[p].ll2_pitch * (g.p[p].h >> 2) * 4);
+    }
+    L.tiles1 = o;
+    o = align256(o + (size_t)g.total_tiles * 4);
+    L.ctiles1 = o;
+    o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
+    L.counters1 = o;
     o = align256(o + 64);
     L.total = o;
     return L;
@@ -196,6 +208,53 @@ int eye_view(const Geom &g, int eye, int *row0, int *rows) {
     return WV_OK;
 }
 
+// The internal stream and events of the overlapped viewport path (created on
+// first use; the stream has the highest priority so that its small kernels
+// take SMs as soon as the running fine pass or resampling frees them).
+cudaError_t ensure_aux(wv_stream *s) {
+    if (s->aux) return cudaSuccess;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, hi);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&s->ev_ready[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_free[k], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+// After work on cs that used the per-viewport buffers of set 0 (or both):
+// later overlapped viewports wait for it before reusing either set.
+void mark_sets_used(wv_stream *s) {
+    if (!s->aux) return;
+    cudaEventRecord(s->ev_free[0], s->cs);
+    cudaEventRecord(s->ev_free[1], s->cs);
+}
+
+// Overlapped viewport decode: footprint, selection and coarse pass on aux
+// into buffer set k (after cs has finished with set k), fine pass on cs.
+int decode_region_overlapped(wv_stream *s, const View &v, const Bands &b, uint32_t gen) {
+    const Geom &g = s->g;
+    const int k = s->slot;
+    s->slot ^= 1;
+    uint32_t *tiles = k ? s->tiles1 : s->tiles, *ctiles = k ? s->ctiles1 : s->ctiles;
+    int *counters = k ? s->counters1 : s->counters;
+    float *ll2[3] = {k ? s->ll2_1[0] : s->ll2[0], k ? s->ll2_1[1] : s->ll2[1], k ? s->ll2_1[2] : s->ll2[2]};
+    cudaError_t e = cudaStreamWaitEvent(s->aux, s->ev_free[k], 0);
+    if (e != cudaSuccess) return WV_ERR_CUDA;
+    launch_footprint(g, v, s->mask, s->tile_gen, s->ctile_gen, gen, counters, s->aux);
+    launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, tiles, ctiles, counters, s->aux);
+    e = launch_decode_coarse(g, s->payload, s->table, b, ll2, s->ll2_pitch, ctiles, counters + 1, s->err, s->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[k], s->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_ready[k], 0);
+    const float *ll2c[3] = {ll2[0], ll2[1], ll2[2]};
+    if (e == cudaSuccess)
+        e = launch_decode_fine(g, s->payload, s->table, b, ll2c, s->ll2_pitch, s->recon, nullptr, -1, tiles,
+                               counters, s->err, s->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_free[k], s->cs);
+    return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
+}
+
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h, int eye) {
     const Geom &g = s->g;
     int row0, rows;
@@ -203,13 +262,17 @@ int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, in
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
     const Bands b = stream_bands(s, frame);
     const uint32_t gen = next_gen(s);
+    if (split_mode(s) && !s->prof && s->overlap && ensure_aux(s) == cudaSuccess)
+        return decode_region_overlapped(s, v, b, gen);
     prof_begin(s, kKFootprint);
     launch_footprint(g, v, s->mask, s->tile_gen, s->ctile_gen, gen, s->counters, s->cs);
     prof_end(s);
     prof_begin(s, kKTiles);
     launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, s->tiles, s->ctiles, s->counters, s->cs);
     prof_end(s);
-    return run_decode(s, b, s->recon, nullptr, -1) == cudaSuccess ? WV_OK : WV_ERR_CUDA;
+    const cudaError_t e = run_decode(s, b, s->recon, nullptr, -1);
+    mark_sets_used(s);
+    return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
 }
 
 }  // namespace wv
@@ -575,6 +638,10 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     }
     s->counters = (int *)(base + L.counters);
     s->err = (int *)(base + L.err);
+    for (int p = 0; p < 3; ++p) s->ll2_1[p] = s->ll2[p] ? (float *)(base + L.ll2_1[p]) : nullptr;
+    s->tiles1 = (uint32_t *)(base + L.tiles1);
+    s->ctiles1 = (uint32_t *)(base + L.ctiles1);
+    s->counters1 = (int *)(base + L.counters1);
     const size_t tcount = (size_t)s->g.num_frames * s->g.nbpf;
     s->table_host.resize(tcount);
     if (is_paper) {
@@ -605,7 +672,8 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.tile_gen, 0, L.total - L.tile_gen, s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.tile_gen, 0, L.err + 64 - L.tile_gen, s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.ll2_1[0], 0, L.total - L.ll2_1[0], s->cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -625,6 +693,12 @@ int wv_set_cuda_stream(wv_stream *s, void *cuda_stream) {
 void wv_close_stream(wv_stream *s) {
     if (!s) return;
     cudaStreamSynchronize(s->cs);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+    }
+    for (cudaEvent_t e : {s->ev_ready[0], s->ev_ready[1], s->ev_free[0], s->ev_free[1]})
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->owns && s->dmem) cudaFree(s->dmem);
     delete s;
@@ -654,6 +728,7 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
     launch_all_tiles(g, plane, s->tiles, s->counters, s->cs);
     if (split_mode(s)) launch_all_ctiles(g, plane, s->ctiles, s->counters, s->cs);
     cudaError_t e = run_decode(s, stream_bands(s, frame), outs, f32, as_float ? plane : -1);
+    mark_sets_used(s);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     return cuda_err(cudaGetLastError());
 }
@@ -683,6 +758,7 @@ int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_
         e = cudaMemcpyAsync(mask_host, m, (size_t)g.cells_x * g.cells_y, cudaMemcpyDeviceToHost, s->cs);
     int cnt = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, s->counters, 4, cudaMemcpyDeviceToHost, s->cs);
+    mark_sets_used(s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (tiles) *tiles = cnt;
     return cuda_err(e);

@@ -295,6 +295,19 @@ struct wv_stream {
     int decode_mode = 0;   // 0: coarse pass + fine pass (levels >= 3), 1: all levels fused
     int *counters = nullptr;
     int *err = nullptr;
+    // A second set of per-viewport buffers (tile lists, counters, LL_2
+    // planes): consecutive viewports alternate between the sets, so the
+    // footprint, selection and coarse pass of a viewport (on the internal
+    // stream `aux`) run while the previous viewport's fine pass and
+    // resampling (on cs) are still executing.  Set 0 is the fields above.
+    uint32_t *tiles1 = nullptr, *ctiles1 = nullptr;
+    int *counters1 = nullptr;
+    float *ll2_1[3] = {nullptr, nullptr, nullptr};
+    int slot = 0;
+    bool overlap = true;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // set k's coarse pass done (aux)
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};    // cs no longer reads set k
     uint64_t n_payload = 0;
     std::vector<int32_t> table_host;
     std::vector<float> qp_host;   // byte quantiser parameters (quant 1), [frame][3][2][2]

@@ -65,6 +65,10 @@ CASES["l1_97"] = (lambda: [tuple(np.ascontiguousarray(pl[:64, :128]) for pl in f
                            for f in synth.equirect_gop(128, 2, seed=52, n_discs=3)],
                   O.Params(128, 64, 3, 1, 1, O.WAVELET_97, 2, 1, 16, 3.0))
 # a constant frame: every detail block is zero and omitted from the stream
+# a fine quantiser step: codes above 8191, so the device keeps them as q
+# (the tile decoder's untranscoded path)
+CASES["wideq97"] = (lambda: synth.equirect_gop(128, 2, seed=9, n_discs=6),
+                    O.Params(128, 128, 3, 1, 3, O.WAVELET_97, 2, 1, 64, 0.008))
 CASES["flat97"] = (lambda: [(np.full((128, 128), 77, np.uint8),)] * 2,
                    O.Params(128, 128, 1, 0, 3, O.WAVELET_97, 2, 1, 32, 4.0))
 

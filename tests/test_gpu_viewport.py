@@ -199,3 +199,33 @@ def test_batch_equals_single_and_bad_requests():
             s1.decode_viewport(*bad, out)
         assert e.value.code == -1
     assert s1.sync_status() == 0 and s2.sync_status() == 0
+
+
+def test_back_to_back_viewports_equal_isolated_decodes():
+    """Consecutive viewports of one stream, enqueued without synchronising:
+    each one's footprint, selection and coarse pass run on the stream's
+    internal second CUDA stream while the previous one's fine pass and
+    resampling run, alternating two sets of tile lists and LL_2 planes; a
+    full-plane decode in between uses the first set.  Every output equals a
+    decode of that viewport alone on a fresh stream."""
+    _, p, _, _ = H.case("yuv97")
+    s = _stream("yuv97")
+    poses = POSES + [(1.1, -0.7, math.radians(75)), (-0.4, 0.9, math.radians(120))]
+    outs = []
+    for k, (yaw, pitch, fov) in enumerate(poses):
+        out = torch.zeros((56, 72, 4), dtype=torch.uint8, device="cuda")
+        s.decode_viewport(k % p.num_frames, yaw, pitch, fov, out)
+        outs.append(out)
+        if k == 3:
+            full = torch.empty((p.height, p.width), dtype=torch.uint8, device="cuda")
+            s.decode_full(1, 0, full)
+    torch.cuda.synchronize()
+    assert s.sync_status() == 0
+    for k, (yaw, pitch, fov) in enumerate(poses):
+        ref = torch.zeros((56, 72, 4), dtype=torch.uint8, device="cuda")
+        _stream("yuv97").decode_viewport(k % p.num_frames, yaw, pitch, fov, ref)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), ref.cpu().numpy())
+    ref_x, ref_u8 = H.oracle_planes("yuv97", 1)[0]
+    diff = full.cpu().numpy() != ref_u8
+    assert not np.any(diff & ~H.near_half(ref_x))
