@@ -104,7 +104,10 @@ int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc,
 
 /* Open a stream: validate the bytes, copy the block table and the coefficient
  * payload to the device and set up per-stream decode scratch (reconstruction
- * planes, mask, tile list).  device_mem is a device buffer of at least
+ * planes, mask, two sets of tile lists and LL_2 planes).  CDF 9/7 dead-zone
+ * codes are rewritten on the device as 2q + sign(q) when every |q| <= 8191
+ * (one pass over the payload; decoded results are unchanged).  The call
+ * synchronises cuda_stream before it returns.  device_mem is a device buffer of at least
  * device_bytes (from wv_stream_query) that the caller owns and keeps alive
  * until wv_close_stream; pass NULL to let the library allocate (and later
  * free) it.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
@@ -142,6 +145,13 @@ const char *wv_strerror(int code);
  *      (Sec. 3.6).
  * Grey streams give R = G = B = Y.  Returns WV_ERR_ARG for a frame outside
  * [0, num_frames), fov outside (0, pi) or a bad image. */
+/* Steps 1, 2 and the coarse levels of step 3 run on a CUDA stream the
+ * library creates for the wv_stream (highest priority), into one of two
+ * sets of scratch buffers that alternate between calls; the remaining
+ * levels wait for them (CUDA event) and run with step 4 on the stream's
+ * CUDA stream.  So consecutive calls overlap, and `out` is complete once the
+ * stream's CUDA stream has passed this call's work, as for every decode
+ * call. */
 int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch,
                        float fov, const wv_image *out);
 
