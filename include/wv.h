@@ -107,10 +107,10 @@ int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc,
  * planes, mask, two sets of tile lists and LL_2 planes).  CDF 9/7 dead-zone
  * codes are rewritten on the device as 2q + sign(q) when every |q| <= 8191
  * (one pass over the payload; decoded results are unchanged).  The call
- * synchronises cuda_stream before it returns.  device_mem is a device buffer of at least
- * device_bytes (from wv_stream_query) that the caller owns and keeps alive
- * until wv_close_stream; pass NULL to let the library allocate (and later
- * free) it.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * synchronises cuda_stream before it returns.  device_mem is a device
+ * buffer of at least device_bytes (from wv_stream_query) that the caller
+ * owns and keeps alive until wv_close_stream; pass NULL to let the library
+ * allocate (and later free) it.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * The host bytes may be freed once this call returns.  On success *out holds
  * the new stream. */
 int wv_open_stream(const void *bytes, size_t n, void *device_mem,
