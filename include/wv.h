@@ -116,6 +116,27 @@ int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc,
 int wv_open_stream(const void *bytes, size_t n, void *device_mem,
                    size_t device_bytes, void *cuda_stream, wv_stream **out);
 
+/* Open flags. */
+#define WV_OPEN_HOST_PAYLOAD 1  /* coefficient store in host memory, see below */
+
+/* wv_stream_query / wv_open_stream with flags (0 = the plain calls).
+ * WV_OPEN_HOST_PAYLOAD keeps the coefficient payload in host memory instead
+ * of copying it to the device: the library copies it into pinned,
+ * device-mapped host memory that it allocates (and frees at close), and the
+ * tile decoder reads the blocks each viewport needs directly from there.
+ * On a Grace-Blackwell node those reads travel over NVLink-C2C, so a video
+ * far larger than HBM can be decoded with only the per-stream scratch on
+ * the device (Sec. 3.5 streams the viewport's coefficients from storage;
+ * here the GPU fetches exactly the coefficients it needs).  Decoded results
+ * are identical to the device-resident store.  device_bytes then excludes
+ * the payload (query with the same flags).  Returns WV_ERR_ARG for unknown
+ * flags and WV_ERR_OOM when pinned host memory cannot be allocated. */
+int wv_stream_query_ex(const void *bytes, size_t n, int flags,
+                       wv_stream_desc *desc, size_t *device_bytes);
+int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem,
+                      size_t device_bytes, void *cuda_stream, int flags,
+                      wv_stream **out);
+
 /* Use another CUDA stream for the following calls on s. */
 int wv_set_cuda_stream(wv_stream *s, void *cuda_stream);
 

@@ -558,6 +558,12 @@ const char *wv_strerror(int code) {
 }
 
 int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc, size_t *device_bytes) {
+    return wv_stream_query_ex(bytes, n, 0, desc, device_bytes);
+}
+
+int wv_stream_query_ex(const void *bytes, size_t n, int flags, wv_stream_desc *desc, size_t *device_bytes) {
+    if (flags & ~WV_OPEN_HOST_PAYLOAD) return WV_ERR_ARG;
+    const bool host_payload = (flags & WV_OPEN_HOST_PAYLOAD) != 0;
     wv_stream_desc d;
     StreamHeader h;
     if (is_paper_stream(bytes, n)) {
@@ -568,7 +574,7 @@ int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc, size_t *d
         if (device_bytes) {
             Geom g;
             build_geom(d, &g);
-            *device_bytes = layout(g, info.n_slots).total;
+            *device_bytes = layout(g, host_payload ? 0 : info.n_slots).total;
         }
         return WV_OK;
     }
@@ -578,15 +584,22 @@ int wv_stream_query(const void *bytes, size_t n, wv_stream_desc *desc, size_t *d
     if (device_bytes) {
         Geom g;
         build_geom(d, &g);
-        *device_bytes = layout(g, h.n_payload).total;
+        *device_bytes = layout(g, host_payload ? 0 : h.n_payload).total;
     }
     return WV_OK;
 }
 
 int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_bytes,
                    void *cuda_stream, wv_stream **out) {
+    return wv_open_stream_ex(bytes, n, device_mem, device_bytes, cuda_stream, 0, out);
+}
+
+int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t device_bytes,
+                      void *cuda_stream, int flags, wv_stream **out) {
     if (!out) return WV_ERR_ARG;
     *out = nullptr;
+    if (flags & ~WV_OPEN_HOST_PAYLOAD) return WV_ERR_ARG;
+    const bool host_payload = (flags & WV_OPEN_HOST_PAYLOAD) != 0;
     wv_stream_desc d;
     StreamHeader h;
     PaperInfo paper;
@@ -606,9 +619,29 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     cudaGetDevice(&s->device);
     s->cs = (cudaStream_t)cuda_stream;
     s->n_payload = h.n_payload;
-    const Layout L = layout(s->g, h.n_payload);
+    const Layout L = layout(s->g, host_payload ? 0 : h.n_payload);
+    const size_t payload_bytes = (size_t)h.n_payload * s->g.block * s->g.block * 2;
+    if (host_payload && payload_bytes) {
+        // the coefficient store in pinned, device-mapped host memory: the
+        // tile decoder reads the blocks a viewport needs from there (on a
+        // Grace-Blackwell node over NVLink-C2C) instead of an HBM copy
+        if (cudaHostAlloc(&s->host_payload, payload_bytes, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return WV_ERR_OOM;
+        }
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, s->host_payload, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(s->host_payload);
+            delete s;
+            return WV_ERR_CUDA;
+        }
+        s->payload = (int16_t *)dp;
+    }
     if (device_mem) {
         if (device_bytes < L.total || ((uintptr_t)device_mem % 256)) {
+            if (s->host_payload) cudaFreeHost(s->host_payload);
             delete s;
             return WV_ERR_OOM;
         }
@@ -616,6 +649,7 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     } else {
         if (cudaMalloc(&s->dmem, L.total) != cudaSuccess) {
             cudaGetLastError();
+            if (s->host_payload) cudaFreeHost(s->host_payload);
             delete s;
             return WV_ERR_OOM;
         }
@@ -623,7 +657,7 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
     }
     s->dbytes = L.total;
     char *base = (char *)s->dmem;
-    s->payload = (int16_t *)(base + L.payload);
+    if (!host_payload) s->payload = (int16_t *)(base + L.payload);
     s->table = (int32_t *)(base + L.table);
     for (int p = 0; p < 3; ++p) s->recon[p] = p < s->g.planes ? (uint8_t *)(base + L.recon[p]) : nullptr;
     s->mask = (uint8_t *)(base + L.mask);
@@ -654,9 +688,11 @@ int wv_open_stream(const void *bytes, size_t n, void *device_mem, size_t device_
                                     cudaMemcpyHostToDevice, s->cs);
     if (e == cudaSuccess && is_paper)
         e = paper_transcode(bytes, n, paper, s->payload, s->cs);
+    else if (e == cudaSuccess && h.n_payload && host_payload)
+        memcpy(s->host_payload, (const char *)bytes + h.payload_off, payload_bytes);
     else if (e == cudaSuccess && h.n_payload)
-        e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off,
-                            h.n_payload * s->g.block * s->g.block * 2, cudaMemcpyHostToDevice, s->cs);
+        e = cudaMemcpyAsync(s->payload, (const char *)bytes + h.payload_off, payload_bytes,
+                            cudaMemcpyHostToDevice, s->cs);
     // 9/7 dead-zone codes become t = 2q + sign(q) on the device when every
     // |q| <= kDzTMax (the tile decoder then needs no sign logic)
     if (e == cudaSuccess && !is_paper && h.n_payload && s->g.wavelet == WV_WAVELET_97 && s->g.quant == 0) {
@@ -699,6 +735,7 @@ void wv_close_stream(wv_stream *s) {
     }
     for (cudaEvent_t e : {s->ev_ready[0], s->ev_ready[1], s->ev_free[0], s->ev_free[1]})
         if (e) cudaEventDestroy(e);
+    if (s->host_payload) cudaFreeHost(s->host_payload);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->owns && s->dmem) cudaFree(s->dmem);
     delete s;

@@ -309,6 +309,7 @@ struct wv_stream {
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // set k's coarse pass done (aux)
     cudaEvent_t ev_free[2] = {nullptr, nullptr};    // cs no longer reads set k
     uint64_t n_payload = 0;
+    void *host_payload = nullptr;   // WV_OPEN_HOST_PAYLOAD: pinned, mapped coefficient store
     std::vector<int32_t> table_host;
     std::vector<float> qp_host;   // byte quantiser parameters (quant 1), [frame][3][2][2]
     // profiling: (kernel id, start, stop) event triples

@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 WV_OK = 0
+WV_OPEN_HOST_PAYLOAD = 1
 ERRORS = {-1: "WV_ERR_ARG", -2: "WV_ERR_FORMAT", -3: "WV_ERR_OOM", -4: "WV_ERR_CUDA",
           -5: "WV_ERR_RANGE", -6: "WV_ERR_TIMEOUT", -7: "WV_ERR_DEVICE"}
 WAVELET_53 = 0
@@ -98,6 +99,8 @@ def _lib():
             "wv_strerror": (ctypes.c_char_p, [c_int]),
             "wv_stream_query": (c_int, [vp, c_size, ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size)]),
             "wv_open_stream": (c_int, [vp, c_size, vp, c_size, vp, ctypes.POINTER(vp)]),
+            "wv_stream_query_ex": (c_int, [vp, c_size, c_int, ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size)]),
+            "wv_open_stream_ex": (c_int, [vp, c_size, vp, c_size, vp, c_int, ctypes.POINTER(vp)]),
             "wv_set_cuda_stream": (c_int, [vp, vp]),
             "wv_close_stream": (None, [vp]),
             "wv_decode_viewport": (c_int, [vp, c_int, fl, fl, fl, ctypes.POINTER(Image)]),
@@ -169,7 +172,8 @@ def _lib():
 def exported_symbols() -> list[str]:
     """Names of the ABI functions the binding resolves (all of include/wv.h)."""
     _lib()
-    return ["wv_strerror", "wv_stream_query", "wv_open_stream", "wv_set_cuda_stream",
+    return ["wv_strerror", "wv_stream_query", "wv_open_stream", "wv_stream_query_ex", "wv_open_stream_ex",
+            "wv_set_cuda_stream",
             "wv_close_stream", "wv_decode_viewport", "wv_decode_viewport_eye", "wv_decode_batch",
             "wv_decode_full",
             "wv_stream_sync_status", "wv_debug_footprint", "wv_debug_project", "wv_resample_at",
@@ -210,29 +214,33 @@ def _image(t) -> Image:
     return Image(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0))
 
 
-def query(data: bytes) -> tuple[dict, int]:
+def query(data: bytes, flags: int = 0) -> tuple[dict, int]:
     d = StreamDesc()
     need = ctypes.c_size_t()
     buf = ctypes.c_char_p(data)
-    _check(_lib().wv_stream_query(buf, len(data), ctypes.byref(d), ctypes.byref(need)), "wv_stream_query")
+    _check(_lib().wv_stream_query_ex(buf, len(data), flags, ctypes.byref(d), ctypes.byref(need)),
+           "wv_stream_query_ex")
     return d.as_dict(), need.value
 
 
 class Stream:
     """An open wavelet video stream resident on the GPU."""
 
-    def __init__(self, data: bytes, cuda_stream=None):
+    def __init__(self, data: bytes, cuda_stream=None, host_payload: bool = False):
+        """host_payload: keep the coefficient store in pinned, device-mapped
+        host memory (WV_OPEN_HOST_PAYLOAD) instead of device memory."""
         import torch
-        self.desc, need = query(data)
+        flags = WV_OPEN_HOST_PAYLOAD if host_payload else 0
+        self.desc, need = query(data, flags)
         # device store supplied by PyTorch's allocator (256-byte aligned)
         self._mem = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
         base = self._mem.data_ptr()
         aligned = (base + 255) & ~255
         self._handle = ctypes.c_void_p()
         self._cuda_stream = cuda_stream
-        _check(_lib().wv_open_stream(ctypes.c_char_p(data), len(data), ctypes.c_void_p(aligned), need,
-                                     ctypes.c_void_p(_cuda_stream_handle(cuda_stream)),
-                                     ctypes.byref(self._handle)), "wv_open_stream")
+        _check(_lib().wv_open_stream_ex(ctypes.c_char_p(data), len(data), ctypes.c_void_p(aligned), need,
+                                        ctypes.c_void_p(_cuda_stream_handle(cuda_stream)), flags,
+                                        ctypes.byref(self._handle)), "wv_open_stream_ex")
         self.device_bytes = need
 
     @property
