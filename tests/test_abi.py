@@ -53,6 +53,28 @@ def test_query_parses_oracle_streams(lib):
         assert need >= len(data) - 128
 
 
+def test_query_with_host_payload_excludes_the_store(lib):
+    """WV_OPEN_HOST_PAYLOAD: the device size drops by at least the stored
+    blocks (host memory holds them); unknown flags are refused."""
+    from paper_2208_10859_gb300 import wv
+    for name in ("yuv97", "ragged53"):
+        _, p, data, st = H.case(name)
+        d0, dev = wv.query(data)
+        d1, host = wv.query(data, wv.WV_OPEN_HOST_PAYLOAD)
+        assert d0 == d1
+        assert dev - host >= st.payload.size * 2
+    with pytest.raises(wv.WVError) as e:
+        wv.query(data, 4)
+    assert e.value.code == -1
+
+
+def test_open_with_unknown_flags_is_refused(lib):
+    _, _, data, _ = H.case("yuv97")
+    h = ctypes.c_void_p()
+    rc = lib.wv_open_stream_ex(ctypes.c_char_p(data), len(data), None, 0, None, 8, ctypes.byref(h))
+    assert rc == -1 and not h.value
+
+
 def test_query_rejects_corrupt_streams(lib):
     from paper_2208_10859_gb300 import wv
     _, _, data, _ = H.case("yuv97")
