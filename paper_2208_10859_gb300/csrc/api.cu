@@ -223,10 +223,22 @@ cudaError_t ensure_aux(wv_stream *s) {
     return e;
 }
 
+// A stream that is ever captured into a CUDA graph decodes serially from
+// then on: the internal stream is not part of a capture, and graph replays
+// must not race with overlapped calls.
+void check_capture(wv_stream *s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->cs, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        s->overlap = false;
+    }
+}
+
 // After work on cs that used the per-viewport buffers of set 0 (or both):
 // later overlapped viewports wait for it before reusing either set.
 void mark_sets_used(wv_stream *s) {
-    if (!s->aux) return;
+    check_capture(s);
+    if (!s->aux || !s->overlap) return;
     cudaEventRecord(s->ev_free[0], s->cs);
     cudaEventRecord(s->ev_free[1], s->cs);
 }
@@ -262,6 +274,7 @@ int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, in
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
     const Bands b = stream_bands(s, frame);
     const uint32_t gen = next_gen(s);
+    check_capture(s);
     if (split_mode(s) && !s->prof && s->overlap && ensure_aux(s) == cudaSuccess)
         return decode_region_overlapped(s, v, b, gen);
     prof_begin(s, kKFootprint);

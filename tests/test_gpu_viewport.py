@@ -229,3 +229,32 @@ def test_back_to_back_viewports_equal_isolated_decodes():
     ref_x, ref_u8 = H.oracle_planes("yuv97", 1)[0]
     diff = full.cpu().numpy() != ref_u8
     assert not np.any(diff & ~H.near_half(ref_x))
+
+
+def test_viewport_captured_in_a_cuda_graph():
+    """A viewport decode captured into a CUDA graph (serial path: the stream
+    then stops overlapping) replays to the same output as a direct decode,
+    and direct decodes on the same stream stay correct afterwards."""
+    _, p, _, _ = H.case("yuv97")
+    s = _stream("yuv97")
+    warm = torch.zeros((40, 56, 4), dtype=torch.uint8, device="cuda")
+    s.decode_viewport(0, 0.2, 0.1, 1.5, warm)          # kernel attributes set outside the capture
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    out = torch.zeros((40, 56, 4), dtype=torch.uint8, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    s.set_cuda_stream(side)
+    with torch.cuda.graph(g, stream=side):
+        s.decode_viewport(1, -1.0, 0.4, 1.7, out)
+    g.replay()
+    torch.cuda.synchronize()
+    ref = torch.zeros_like(out)
+    _stream("yuv97").decode_viewport(1, -1.0, 0.4, 1.7, ref)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    s.set_cuda_stream(torch.cuda.current_stream())
+    after = torch.zeros_like(out)
+    s.decode_viewport(0, 0.2, 0.1, 1.5, after)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(after.cpu().numpy(), warm.cpu().numpy())
+    assert s.sync_status() == 0
