@@ -172,7 +172,9 @@ const char *wv_strerror(int code);
  * levels wait for them (CUDA event) and run with step 4 on the stream's
  * CUDA stream.  So consecutive calls overlap, and `out` is complete once the
  * stream's CUDA stream has passed this call's work, as for every decode
- * call. */
+ * call.  A call made while the stream's CUDA stream is being captured into
+ * a CUDA graph records every step on that stream, and the wv_stream decodes
+ * serially from then on (graph replays never race with later calls). */
 int wv_decode_viewport(wv_stream *s, int frame, float yaw, float pitch,
                        float fov, const wv_image *out);
 
