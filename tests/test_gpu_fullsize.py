@@ -87,3 +87,38 @@ def test_full_size_viewports(full):
         # 1 / cos(latitude) (11 % of the pixels for a view reaching 93 deg)
         assert int(np.sum(flag)) <= 0.15 * idx.size
     assert s.sync_status() == 0
+
+
+def test_full_size_batch_and_host_store_equal_the_loop(full):
+    """The batch engine (independent and shared decode targets) and the
+    host-resident store give the same viewports as the per-viewport loop on
+    the full-size stream."""
+    from paper_2208_10859_gb300 import wv
+    p, data, _ = full
+    s = wv.Stream(data)
+    poses = synth.random_poses(64, seed=3)[:6]
+    loop = []
+    for i, (yaw, pitch) in enumerate(poses):
+        o = torch.zeros((OUT, OUT, 4), dtype=torch.uint8, device="cuda")
+        s.decode_viewport(i % 2, yaw, pitch, FOV, o)
+        loop.append(o)
+    torch.cuda.synchronize()
+    for share in (False, True):
+        b = wv.Batch()
+        b.set_sharing(share)
+        reqs = [wv.ViewRequest(s, i % 2, yaw, pitch, FOV, torch.zeros((OUT, OUT, 4), dtype=torch.uint8,
+                                                                        device="cuda"))
+                for i, (yaw, pitch) in enumerate(poses)]
+        b.decode(reqs)
+        torch.cuda.synchronize()
+        assert b.sync_status() == 0
+        for r, ref in zip(reqs, loop):
+            assert torch.equal(r.out, ref)
+        b.close()
+    h = wv.Stream(data, host_payload=True)
+    for i, (yaw, pitch) in enumerate(poses[:2]):
+        o = torch.zeros((OUT, OUT, 4), dtype=torch.uint8, device="cuda")
+        h.decode_viewport(i % 2, yaw, pitch, FOV, o)
+        torch.cuda.synchronize()
+        assert torch.equal(o, loop[i])
+    assert s.sync_status() == 0 and h.sync_status() == 0
