@@ -404,6 +404,7 @@ void wv_server_close(wv_server *sv);
  * is used by one host thread at a time. */
 typedef struct wv_cnn wv_cnn;
 
+/* Number of floats in the parameter array (all layers). */
 size_t wv_cnn_param_count(void);
 
 /* Create a network with the given parameters (host, wv_cnn_param_count()
@@ -506,6 +507,9 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out);
  * filter supports, symmetric extension), restricted to stored blocks,
  * 2 bytes per coefficient, summed over the coefficient frames the
  * inter-frame rebuild reads.  Host computation. */
+int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
+                  unsigned long long *bytes);
+
 /* As wv_cone_bytes with foveation: fovea_host (one byte per mask cell, host;
  * bit 0 keeps the level-1 details of the cell, bit 1 the level-2 details;
  * NULL keeps everything) drops the detail coefficients of levels 1 and 2
@@ -521,9 +525,6 @@ int wv_cone_bytes_fovea(wv_stream *s, int frame, const uint8_t *mask_host,
  * cell over the planes). */
 int wv_request_bytes(const wv_request *r, unsigned long long *cone, unsigned long long *region);
 
-int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
-                  unsigned long long *bytes);
-
 /* Per-kernel device time of the calls since the last wv_profile_begin,
  * measured with CUDA events recorded on the stream's CUDA stream around
  * each launch. */
@@ -533,6 +534,9 @@ typedef struct {
     int tiles;           /* tiles decoded by the last viewport */
 } wv_profile;
 
+/* Start recording: the following decode calls on s record events around
+ * each launch and run all their steps serially on the stream's CUDA stream
+ * (no overlap between viewports, so that each interval is one kernel). */
 int wv_profile_begin(wv_stream *s);
 /* Synchronises, sums the recorded event intervals into *out and stops. */
 int wv_profile_end(wv_stream *s, wv_profile *out);
