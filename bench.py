@@ -709,13 +709,19 @@ def run_ours(args):
     prof = s.profile_end()
     dec_ms = prof["decode_coarse"][0] + prof["decode_fine"][0]
     dec_n = prof["decode_fine"][1]
-    # the other tile-decode organisation (all levels fused per tile), for comparison
+    # the other tile-decode organisations on square tiles, for comparison:
+    # all levels fused per tile (mode 1), coarse pass + square fine pass (mode 2)
     s.set_decode_mode(1)
     s.profile_begin()
     step()
     prof_fused = s.profile_end()
+    s.set_decode_mode(2)
+    s.profile_begin()
+    step()
+    prof_sq = s.profile_end()
     s.set_decode_mode(0)
     fused_ms = prof_fused["decode_fine"][0] / max(1, prof_fused["decode_fine"][1])
+    sq_ms = {k: prof_sq[k][0] / max(1, prof_sq[k][1]) for k in ("decode_coarse", "decode_fine")}
     alg_dec = sum(cone) + sum(region)   # per pass over the poses
     achieved = alg_dec * args.steps / (dec_ms / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
@@ -830,7 +836,8 @@ def run_ours(args):
             "kernel_ms_per_launch": kernel_ms,
             "batch_engine_same_workload": engine,
             "decode_ms_per_viewport": {"split (coarse + fine)": dec_ms / max(1, dec_n),
-                                       "fused (all levels per tile)": fused_ms},
+                                       "fused (all levels per square tile)": fused_ms,
+                                       "square tiles (coarse + fine)": sq_ms},
             "viewport_bytes": {"cone_coef_mean": sum(cone) / len(cone), "region_mean": sum(region) / len(region),
                                "per_pose_decode_alg": ([c + r for c, r in zip(cone, region)]
                                                        if len(poses) <= 8 else None),

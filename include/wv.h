@@ -544,12 +544,16 @@ int wv_profile_end(wv_stream *s, wv_profile *out);
 /* Number of kernel launches a wv_decode_viewport call on s makes. */
 int wv_launches_per_viewport(const wv_stream *s);
 
-/* Tile-decode organisation for streams of three or more levels: mode 0
- * (default) decodes levels L..3 of the needed coarse tiles into float LL_2
- * planes in one kernel and levels 2..1 of the needed output tiles in a
- * second; mode 1 runs all levels of each output tile in one kernel, repeating
- * the coarse levels per tile.  Results are identical up to float rounding
- * order for 9/7 and bit-exact for 5/3. */
+/* Tile-decode organisation.  Mode 0 (default): levels L..3 of the needed
+ * coarse tiles go into float LL_2 planes in one kernel (streams of three or
+ * more levels), then levels 2 and 1 of the needed output tiles in a second;
+ * for dead-zone streams of two or more levels the second kernel streams each
+ * 224-column strip of the region down its rows in one warp (strip tiles),
+ * otherwise it decodes square 128-sample tiles.  Mode 1: all levels of each
+ * square output tile in one kernel, repeating the coarse levels per tile.
+ * Mode 2: the coarse pass, then levels 2 and 1 of square output tiles (mode
+ * 0 for streams without strip tiles).  Results are identical up to float
+ * rounding order for 9/7 and bit-exact for 5/3. */
 int wv_set_decode_mode(wv_stream *s, int mode);
 
 /* ---------------------------------------------------------------------------

@@ -31,7 +31,14 @@ namespace {
 
 enum Kernel { kKFootprint = 0, kKTiles = 1, kKCoarse = 2, kKFine = 3, kKResample = 4 };
 
-bool split_mode(const wv_stream *s) { return s->decode_mode == 0 && s->g.levels >= 3; }
+// Geometry of the stream's viewport and whole-plane decodes in its current
+// decode mode: 0 = the default geometry (strip tiles for the streams the
+// strip kernel decodes), 1 and 2 = square tiles.
+const Geom &active_geom(const wv_stream *s) { return s->decode_mode == 0 ? s->g : s->gsq; }
+// Strip fine pass (levels 2 and 1 streamed down strips, strip.cu).
+bool strip_mode(const wv_stream *s) { return s->decode_mode == 0 && s->g.strip; }
+// Coarse pass (levels L..3 into LL_2 planes) before the fine pass.
+bool split_mode(const wv_stream *s) { return s->decode_mode != 1 && s->g.levels >= 3; }
 
 // Coefficient frames of `frame` with the byte quantiser's parameters of the
 // paper-faithful format (quant 1).
@@ -88,12 +95,26 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
     return WV_OK;
 }
 
+// Both geometries of a stream: square tiles always, strip tiles where the
+// strip kernel applies (else a copy of the square geometry).
+int stream_geoms(const wv_stream_desc &d, uint64_t n_payload, Geom *g, Geom *gsq) {
+    const int rc = build_geom(d, gsq);
+    if (rc != WV_OK) return rc;
+    if (strip_eligible(d, n_payload)) return build_geom_strip(d, g);
+    *g = *gsq;
+    return WV_OK;
+}
+
 struct Layout {
     size_t payload, table, recon[3], ll2[3], mask, tiles, ctiles, tile_gen, ctile_gen, counters, err;
     size_t ll2_1[3], tiles1, ctiles1, counters1, total;   // the second per-viewport set
 };
 
-Layout layout(const Geom &g, uint64_t n_payload) {
+// Device layout of a stream; tile lists and stamps hold the larger tile count
+// of the two geometries.
+Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
+    Geom g = g0;
+    g.total_tiles = std::max(g0.total_tiles, gsq.total_tiles);
     Layout L;
     size_t o = 0;
     L.payload = o;
@@ -170,9 +191,22 @@ int check_image(const wv_image *o) {
 // Tile decode of the selected tiles: a coarse pass (levels L..3 into LL_2
 // planes) followed by a fine pass (levels 2 and 1), or all levels in one
 // pass when the stream has fewer than three levels or mode 1 is set.
+// The fine pass (levels 2 and 1) of the listed tiles: strips, or square tiles
+// reading LL_2 from the planes.  ll2 == null: two-level streams (strips only).
+cudaError_t launch_fine(wv_stream *s, const Bands &b, const float *const *ll2, uint8_t *const *out_u8,
+                        float *f32, int f32_plane, const uint32_t *tiles, int *counters,
+                        cudaStream_t cs) {
+    const Geom &g = active_geom(s);
+    if (strip_mode(s))
+        return launch_decode_strips(g, s->payload, s->table, b, ll2, s->ll2_pitch, out_u8, f32, f32_plane, tiles,
+                                    counters, s->err, cs);
+    return launch_decode_fine(g, s->payload, s->table, b, ll2, s->ll2_pitch, out_u8, f32, f32_plane, tiles,
+                              counters, s->err, cs);
+}
+
 cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, float *f32,
                        int f32_plane) {
-    const Geom &g = s->g;
+    const Geom &g = active_geom(s);
     cudaError_t e;
     if (split_mode(s)) {
         prof_begin(s, kKCoarse);
@@ -182,14 +216,16 @@ cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, flo
         if (e != cudaSuccess) return e;
         const float *ll2c[3] = {s->ll2[0], s->ll2[1], s->ll2[2]};
         prof_begin(s, kKFine);
-        e = launch_decode_fine(g, s->payload, s->table, b, ll2c, s->ll2_pitch, out_u8, f32,
-                               f32_plane, s->tiles, s->counters, s->err, s->cs);
+        e = launch_fine(s, b, ll2c, out_u8, f32, f32_plane, s->tiles, s->counters, s->cs);
         prof_end(s);
         return e;
     }
     prof_begin(s, kKFine);
-    e = launch_decode_tiles(g, s->payload, s->table, b, out_u8, f32, f32_plane, s->tiles,
-                            s->counters, s->err, s->cs);
+    if (strip_mode(s))   // two levels: LL_2 is the stream's LL band
+        e = launch_fine(s, b, nullptr, out_u8, f32, f32_plane, s->tiles, s->counters, s->cs);
+    else
+        e = launch_decode_tiles(g, s->payload, s->table, b, out_u8, f32, f32_plane, s->tiles,
+                                s->counters, s->err, s->cs);
     prof_end(s);
     return e;
 }
@@ -246,7 +282,7 @@ void mark_sets_used(wv_stream *s) {
 // Overlapped viewport decode: footprint, selection and coarse pass on aux
 // into buffer set k (after cs has finished with set k), fine pass on cs.
 int decode_region_overlapped(wv_stream *s, const View &v, const Bands &b, uint32_t gen) {
-    const Geom &g = s->g;
+    const Geom &g = active_geom(s);
     const int k = s->slot;
     s->slot ^= 1;
     uint32_t *tiles = k ? s->tiles1 : s->tiles, *ctiles = k ? s->ctiles1 : s->ctiles;
@@ -260,15 +296,13 @@ int decode_region_overlapped(wv_stream *s, const View &v, const Bands &b, uint32
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[k], s->aux);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_ready[k], 0);
     const float *ll2c[3] = {ll2[0], ll2[1], ll2[2]};
-    if (e == cudaSuccess)
-        e = launch_decode_fine(g, s->payload, s->table, b, ll2c, s->ll2_pitch, s->recon, nullptr, -1, tiles,
-                               counters, s->err, s->cs);
+    if (e == cudaSuccess) e = launch_fine(s, b, ll2c, s->recon, nullptr, -1, tiles, counters, s->cs);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_free[k], s->cs);
     return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
 }
 
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h, int eye) {
-    const Geom &g = s->g;
+    const Geom &g = active_geom(s);
     int row0, rows;
     if (eye_view(g, eye, &row0, &rows) != WV_OK) return WV_ERR_ARG;
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
@@ -417,9 +451,14 @@ void fovea_bits_host(const Geom &g, double yaw, double pitch, const wv_request &
 
 namespace wv {
 
-int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
+namespace {
+
+// Common geometry of both tile organisations: output tiles tw x th (plane
+// pixels, multiples of the 32-pixel mask cell, and of 16 chroma pixels) and
+// coarse tiles of ctile LL_2 samples.
+int build_geom_tiles(const wv_stream_desc &d, Geom *g, int tw, int th, int strip, int ctile) {
     memset(g, 0, sizeof(*g));
-    if ((tile != 64 && tile != 128) || (ctile != 32 && ctile != 64)) return WV_ERR_ARG;
+    if (tw % kCell || th % kCell || tw <= 0 || th <= 0 || (ctile != 32 && ctile != 64)) return WV_ERR_ARG;
     if (d.planes != 1 && d.planes != 3) return WV_ERR_ARG;
     if (d.chroma_420 != 0 && d.chroma_420 != 1) return WV_ERR_ARG;
     if (d.levels < 1 || d.levels > kMaxLevels) return WV_ERR_ARG;
@@ -450,8 +489,18 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     g->stereo = d.stereo;
     g->cells_x = d.width / kCell;
     g->cells_y = d.height / kCell;
-    g->tile = tile;
+    g->tw = tw;
+    g->th = th;
+    g->strip = strip;
     g->ctile = ctile;
+    // LL_2 window of an output tile: the square tile kernel's fine pass reads
+    // its LL_2 window q t - 3 .. q t + q + 2 (q = tile / 4, the 9/7 halo of
+    // two levels); a strip's level-2 lanes read LL_2 columns X0/4 - 4 ..
+    // X0/4 + 59 and its level-2 row pairs LL_2 rows Y0/4 - 3 .. Y0/4 + th/4 + 2
+    g->wx0 = strip ? -4 : -3;
+    g->wx1 = strip ? 59 : tw / 4 + 2;
+    g->wy0 = -3;
+    g->wy1 = th / 4 + 2;
     int id = 0;
     g->total_tiles = 0;
     g->total_ctiles = 0;
@@ -475,11 +524,9 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
                 pg.base[l][s] = id;
                 id += pg.nbx[l] * pg.nby[l];
             }
-        pg.tiles_x = (pg.w + tile - 1) / tile;
-        pg.tiles_y = (pg.h + tile - 1) / tile;
+        pg.tiles_x = (pg.w + tw - 1) / tw;
+        pg.tiles_y = (pg.h + th - 1) / th;
         g->total_tiles += pg.tiles_x * pg.tiles_y;
-        pg.tile_shift = 0;   // a tile spans tile * sub / 32 mask cells per side
-        while ((kCell << pg.tile_shift) < tile * pg.sub) ++pg.tile_shift;
         pg.ll2_pitch = (((pg.w >> 2) + 7) / 8) * 8;
         if (d.levels >= 3) {
             pg.ctiles_x = ((pg.w >> 2) + ctile - 1) / ctile;
@@ -489,6 +536,32 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
     }
     g->nbpf = id;
     return WV_OK;
+}
+
+}  // namespace
+
+int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
+    if (tile != 64 && tile != 128) {
+        memset(g, 0, sizeof(*g));
+        return WV_ERR_ARG;
+    }
+    return build_geom_tiles(d, g, tile, tile, 0, ctile);
+}
+
+// The strip kernel decodes levels 2 and 1 of dead-zone streams (LL_2 from the
+// coarse pass, or the LL band itself at two levels) and addresses the payload
+// with 32-bit element offsets.
+bool strip_eligible(const wv_stream_desc &d, uint64_t n_payload) {
+    return d.levels >= 2 && d.quant == 0 &&
+           n_payload * (uint64_t)d.block * (uint64_t)d.block < (1ull << 32);
+}
+
+int build_geom_strip(const wv_stream_desc &d, Geom *g, int th, int ctile) {
+    if (th % kCell || th < 32 || th > 256) {
+        memset(g, 0, sizeof(*g));
+        return WV_ERR_ARG;
+    }
+    return build_geom_tiles(d, g, kStripW, th, 1, ctile);
 }
 
 Bands frame_bands(const Geom &g, int frame) {
@@ -585,9 +658,9 @@ int wv_stream_query_ex(const void *bytes, size_t n, int flags, wv_stream_desc *d
         if (rc != WV_OK) return rc;
         if (desc) *desc = d;
         if (device_bytes) {
-            Geom g;
-            build_geom(d, &g);
-            *device_bytes = layout(g, host_payload ? 0 : info.n_slots).total;
+            Geom g, gsq;
+            stream_geoms(d, info.n_slots, &g, &gsq);
+            *device_bytes = layout(g, gsq, host_payload ? 0 : info.n_slots).total;
         }
         return WV_OK;
     }
@@ -595,9 +668,9 @@ int wv_stream_query_ex(const void *bytes, size_t n, int flags, wv_stream_desc *d
     if (rc != WV_OK) return rc;
     if (desc) *desc = d;
     if (device_bytes) {
-        Geom g;
-        build_geom(d, &g);
-        *device_bytes = layout(g, host_payload ? 0 : h.n_payload).total;
+        Geom g, gsq;
+        stream_geoms(d, h.n_payload, &g, &gsq);
+        *device_bytes = layout(g, gsq, host_payload ? 0 : h.n_payload).total;
     }
     return WV_OK;
 }
@@ -627,12 +700,12 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return WV_ERR_CUDA;
     wv_stream *s = new (std::nothrow) wv_stream();
     if (!s) return WV_ERR_OOM;
-    build_geom(d, &s->g);
+    stream_geoms(d, h.n_payload, &s->g, &s->gsq);
     s->desc = d;
     cudaGetDevice(&s->device);
     s->cs = (cudaStream_t)cuda_stream;
     s->n_payload = h.n_payload;
-    const Layout L = layout(s->g, host_payload ? 0 : h.n_payload);
+    const Layout L = layout(s->g, s->gsq, host_payload ? 0 : h.n_payload);
     const size_t payload_bytes = (size_t)h.n_payload * s->g.block * s->g.block * 2;
     if (host_payload && payload_bytes) {
         // the coefficient store in pinned, device-mapped host memory: the
@@ -718,6 +791,7 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
         if (e == cudaSuccess && max_abs <= kDzTMax) {
             e = payload_to_deadzone_t(s->payload, count, s->cs);
             s->g.dz_t = 1;
+            s->gsq.dz_t = 1;
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
@@ -768,7 +842,7 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
     if (!s || frame < 0 || frame >= s->g.num_frames || plane < 0 || plane >= s->g.planes)
         return WV_ERR_ARG;
     if (!dptr && as_float) return WV_ERR_ARG;
-    const Geom &g = s->g;
+    const Geom &g = active_geom(s);
     uint8_t *outs[3] = {s->recon[0], s->recon[1], s->recon[2]};
     float *f32 = nullptr;
     if (dptr) {
@@ -795,7 +869,7 @@ int wv_stream_sync_status(wv_stream *s) {
 int wv_debug_footprint(wv_stream *s, float yaw, float pitch, float fov, int out_w, int out_h,
                        uint8_t *mask_host, int *tiles) {
     if (!s || out_w <= 0 || out_h <= 0 || !(fov > 0.f && fov < 3.14159f)) return WV_ERR_ARG;
-    const Geom &g = s->g;
+    const Geom &g = active_geom(s);
     int row0, rows;
     eye_view(g, 0, &row0, &rows);
     const View v = make_view(yaw, pitch, fov, out_w, out_h, g.p[0].w, rows, row0);
@@ -901,7 +975,7 @@ int wv_launches_per_viewport(const wv_stream *s) {
 }
 
 int wv_set_decode_mode(wv_stream *s, int mode) {
-    if (!s || mode < 0 || mode > 1) return WV_ERR_ARG;
+    if (!s || mode < 0 || mode > 2) return WV_ERR_ARG;
     s->decode_mode = mode;
     return WV_OK;
 }

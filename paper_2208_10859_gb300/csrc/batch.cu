@@ -210,7 +210,7 @@ TileArgs pass_args(const Surface &S, char *base, int *err, bool coarse) {
     if (coarse) {
         a.l_top = S.g.levels;
         a.l_bot = 3;
-        a.tile = S.g.ctile;
+        a.tw = a.th = S.g.ctile;
         for (int p = 0; p < S.g.planes; ++p) {
             a.ll_out[p] = (float *)(base + S.ll2[p]);
             a.ll_out_pitch[p] = S.g.p[p].ll2_pitch;
@@ -218,7 +218,8 @@ TileArgs pass_args(const Surface &S, char *base, int *err, bool coarse) {
     } else {
         a.l_top = split ? 2 : S.g.levels;
         a.l_bot = 1;
-        a.tile = S.g.tile;
+        a.tw = S.g.tw;
+        a.th = S.g.th;
         for (int p = 0; p < S.g.planes; ++p) {
             a.out_u8[p] = (uint8_t *)(base + S.recon[p]);
             if (split) {

@@ -13,8 +13,8 @@ namespace {
 
 // Coarse tiles [c_lo, c_hi] (ctile samples of LL_2) holding LL_2 indices
 // [lo, hi] of a subband of n2 samples after whole-sample symmetric extension.
-// A tile t of side T needs the LL_2 window [q t - 3, q t + q + 2] (q = T / 4;
-// 9/7 halo, the 5/3 window is narrower).
+// An output tile's LL_2 window is given by the geometry (Geom::wx0 ..
+// Geom::wy1: the 9/7 halo of levels 2 and 1; the 5/3 window is narrower).
 __device__ __forceinline__ void coarse_span(int lo, int hi, int n2, int ctile, int &c_lo,
                                             int &c_hi) {
     int a = max(lo, 0), b = min(hi, n2 - 1);
@@ -93,13 +93,14 @@ __device__ __forceinline__ void stamp_cell(const Geom &g, int cx, int cy, uint32
     int base = 0, cbase = 0;
     for (int p = 0; p < g.planes; ++p) {
         const PlaneGeom &pg = g.p[p];
-        const int tx = cx >> pg.tile_shift, ty = cy >> pg.tile_shift;
+        const int cw = kCell / pg.sub;   // plane pixels per cell side (tile sides are multiples)
+        const int tx = cx * cw / g.tw, ty = cy * cw / g.th;
         tile_gen[base + ty * pg.tiles_x + tx] = gen;
         if (pg.ctiles_x > 0) {
             int cx0, cx1, cy0, cy1;
-            const int q = g.tile / 4;   // LL_2 samples per tile side
-            coarse_span(q * tx - 3, q * tx + q + 2, pg.w >> 2, g.ctile, cx0, cx1);
-            coarse_span(q * ty - 3, q * ty + q + 2, pg.h >> 2, g.ctile, cy0, cy1);
+            const int qx = g.tw / 4, qy = g.th / 4;   // LL_2 samples per tile side
+            coarse_span(qx * tx + g.wx0, qx * tx + g.wx1, pg.w >> 2, g.ctile, cx0, cx1);
+            coarse_span(qy * ty + g.wy0, qy * ty + g.wy1, pg.h >> 2, g.ctile, cy0, cy1);
             for (int y = cy0; y <= cy1; ++y)
                 for (int x = cx0; x <= cx1; ++x) ctile_gen[cbase + y * pg.ctiles_x + x] = gen;
         }
@@ -141,7 +142,7 @@ __global__ void k_footprint(View v, Frustum f, Geom g, uint8_t *__restrict__ mas
                             uint32_t gen, int *counters) {
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
     const int cy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (cx == 0 && cy == 0) counters[0] = counters[1] = 0;   // tile counts of this viewport
+    if (cx == 0 && cy == 0) counters[0] = counters[1] = counters[2] = 0;   // tile counts of this viewport
     if (cx >= g.cells_x || cy >= g.cells_y) return;
     const bool hit = cell_needed_eye(v, f, g.p[0].w, cx, cy);
     mask[cy * g.cells_x + cx] = hit ? 1 : 0;
@@ -244,9 +245,12 @@ __global__ void k_select_batch(const SurfaceJob *__restrict__ surfs, BatchLists 
 }
 
 __global__ void k_all_tiles(int plane, int tiles_x, int tiles_y, uint32_t *tiles,
-                            int *count) {
+                            int *count, int *work) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *count = tiles_x * tiles_y;
+    if (t == 0) {
+        *count = tiles_x * tiles_y;
+        if (work) *work = 0;
+    }
     if (t >= tiles_x * tiles_y) return;
     tiles[t] = ((uint32_t)plane << 28) | ((uint32_t)(t / tiles_x) << 14) | (uint32_t)(t % tiles_x);
 }
@@ -297,14 +301,14 @@ void launch_all_tiles(const Geom &g, int plane, uint32_t *tiles, int *counters,
                       cudaStream_t cs) {
     const int n = g.p[plane].tiles_x * g.p[plane].tiles_y;
     k_all_tiles<<<(n + 255) / 256, 256, 0, cs>>>(plane, g.p[plane].tiles_x, g.p[plane].tiles_y,
-                                                 tiles, &counters[0]);
+                                                 tiles, &counters[0], &counters[2]);
 }
 
 void launch_all_ctiles(const Geom &g, int plane, uint32_t *ctiles, int *counters,
                        cudaStream_t cs) {
     const int n = g.p[plane].ctiles_x * g.p[plane].ctiles_y;
     k_all_tiles<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, cs>>>(
-        plane, g.p[plane].ctiles_x, g.p[plane].ctiles_y, ctiles, &counters[1]);
+        plane, g.p[plane].ctiles_x, g.p[plane].ctiles_y, ctiles, &counters[1], nullptr);
 }
 
 void launch_project(const View &v, float *uv, cudaStream_t cs) {

@@ -32,20 +32,11 @@
 #include <mutex>
 #include <tuple>
 
-#include "wv_impl.h"
+#include "codes.cuh"
 
 namespace wv {
 
 namespace {
-
-// CDF 9/7 lifting factorisation (Daubechies & Sweldens 1998; JPEG2000 Part 1
-// irreversible wavelet): analysis lifts with alpha, beta, gamma, delta and
-// scales the low band by 1/K and the high band by K.
-constexpr float kAlpha = -1.586134342059924f;
-constexpr float kBeta = -0.052980118572961f;
-constexpr float kGamma = 0.882911075530934f;
-constexpr float kDelta = 0.443506852043971f;
-constexpr double kK = 1.230174104914001;
 
 template <int WAV>
 struct Traits;
@@ -63,13 +54,6 @@ struct Traits<1> {   // CDF 9/7, float lifting
 };
 
 __device__ __host__ __forceinline__ int floor8(int x) { return x & ~7; }
-
-// Index of coefficient k of a subband of n coefficients after whole-sample
-// symmetric extension of the interleaved line (low band: even positions,
-// high band: odd positions).
-__device__ __forceinline__ int refl_sub(int k, int n, int high) {
-    return reflect_idx(2 * k + high, 2 * n) >> 1;
-}
 
 // ---- per-level geometry ----------------------------------------------------
 
@@ -115,18 +99,6 @@ __device__ __forceinline__ LevelGeo make_level(int l, Range ox, Range oy, int pw
 }
 
 // ---- dequantisation + inter-frame rebuild of 8 coefficients ----------------
-
-__device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xffffu); }
-__device__ __forceinline__ int hi16(uint32_t w) { return (int)(int16_t)(w >> 16); }
-
-// Both int16 halves of a word as floats, exactly and without a conversion
-// instruction: each half, biased to unsigned (v + 2^15), becomes the low
-// mantissa bits of 2^23, and 2^23 + 2^15 is subtracted.
-__device__ __forceinline__ void halves_to_float(uint32_t w, float &lo, float &hi) {
-    const uint32_t x = w ^ 0x80008000u;
-    lo = __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8421376.0f;
-    hi = __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8421376.0f;
-}
 
 template <int NB>
 struct Raw {
@@ -673,8 +645,8 @@ __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float 
     const int nout_x = pg.w >> (a.l_bot - 1), nout_y = pg.h >> (a.l_bot - 1);
     // output ranges of every level (level l - 1 coordinates), l_bot upward
     Range ox[kMaxLevels + 2], oy[kMaxLevels + 2];
-    ox[a.l_bot] = {tx * a.tile, min((tx + 1) * a.tile, nout_x) - 1};
-    oy[a.l_bot] = {ty * a.tile, min((ty + 1) * a.tile, nout_y) - 1};
+    ox[a.l_bot] = {tx * a.tw, min((tx + 1) * a.tw, nout_x) - 1};
+    oy[a.l_bot] = {ty * a.th, min((ty + 1) * a.th, nout_y) - 1};
     for (int l = a.l_bot + 1; l <= a.l_top; ++l) {
         ox[l] = {(ox[l - 1].lo >> 1) - H, (ox[l - 1].hi >> 1) + H};
         oy[l] = {(oy[l - 1].lo >> 1) - H, (oy[l - 1].hi >> 1) + H};
@@ -861,31 +833,43 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-// Shared-memory needs (floats) of A and P for tiles of side `tile` at level
-// l_bot - 1 synthesised from l_top.  Window sizes depend on the tile origin
-// only modulo 2^(l_top - l_bot + 4) * tile, which the scan covers.
-void smem_needs(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats) {
+// Shared-memory needs (floats) of A and P for tiles of tw x th outputs at
+// level l_bot - 1 synthesised from l_top: the largest row count over tile
+// origins in y times the largest row stride over origins in x (A), and the
+// largest output row count times the largest P stride (P).  Window sizes
+// depend on the tile origin only modulo 2^(l_top - l_bot + 4) * tile, which
+// the scan covers.
+void smem_needs(int wavelet, int l_top, int l_bot, int tw, int th, int *a_floats, int *p_floats) {
     const int H = wavelet == WV_WAVELET_97 ? 2 : 1;
-    int amax = 0, pmax = 0;
-    for (int origin = 0; origin < 64 * tile; origin += tile) {
-        Range outs[kMaxLevels + 2];
-        outs[l_bot] = {origin, origin + tile - 1};
-        for (int l = l_bot + 1; l <= l_top; ++l)
-            outs[l] = {(outs[l - 1].lo >> 1) - H, (outs[l - 1].hi >> 1) + H};
-        for (int l = l_bot; l <= l_top; ++l) {
-            const Range ox = outs[l];
-            const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
-            const int kx0 = floor8(kx.lo);
-            const int rows = 2 * (kx.hi - kx.lo + 1);
-            const int ja4 = (ox.lo - 2 * kx0) & ~15;
-            const int sa = ((ox.hi - 2 * kx0 + 1) - ja4 + 15) & ~15;
-            if (rows * sa > amax) amax = rows * sa;
-            if (l > l_bot) {
-                const PLayout pn = p_layout(ox);
-                const int p = (ox.hi - ox.lo + 1) * pn.stride;
-                if (p > pmax) pmax = p;
+    int rows_max[kMaxLevels + 2] = {}, sa_max[kMaxLevels + 2] = {}, oy_max[kMaxLevels + 2] = {},
+        ps_max[kMaxLevels + 2] = {};
+    for (int axis = 0; axis < 2; ++axis) {
+        const int tile = axis == 0 ? tw : th;
+        for (int origin = 0; origin < 64 * tile; origin += tile) {
+            Range outs[kMaxLevels + 2];
+            outs[l_bot] = {origin, origin + tile - 1};
+            for (int l = l_bot + 1; l <= l_top; ++l)
+                outs[l] = {(outs[l - 1].lo >> 1) - H, (outs[l - 1].hi >> 1) + H};
+            for (int l = l_bot; l <= l_top; ++l) {
+                const Range ox = outs[l];
+                const Range kx = {(ox.lo >> 1) - H, (ox.hi >> 1) + H};
+                if (axis == 0) {
+                    const int kx0 = floor8(kx.lo);
+                    const int ja4 = (ox.lo - 2 * kx0) & ~15;
+                    const int sa = ((ox.hi - 2 * kx0 + 1) - ja4 + 15) & ~15;
+                    sa_max[l] = std::max(sa_max[l], sa);
+                    ps_max[l] = std::max(ps_max[l], p_layout(ox).stride);
+                } else {
+                    rows_max[l] = std::max(rows_max[l], 2 * (kx.hi - kx.lo + 1));
+                    oy_max[l] = std::max(oy_max[l], ox.hi - ox.lo + 1);
+                }
             }
         }
+    }
+    int amax = 0, pmax = 0;
+    for (int l = l_bot; l <= l_top; ++l) {
+        amax = std::max(amax, rows_max[l] * sa_max[l]);
+        if (l > l_bot) pmax = std::max(pmax, oy_max[l] * ps_max[l]);
     }
     *a_floats = amax;
     *p_floats = pmax;
@@ -895,14 +879,14 @@ std::mutex g_cache_mutex;
 
 }  // namespace
 
-void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats) {
-    static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> cache;
+void smem_needs_cached(int wavelet, int l_top, int l_bot, int tw, int th, int *a_floats, int *p_floats) {
+    static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
     std::lock_guard<std::mutex> lock(g_cache_mutex);
-    const auto key = std::make_tuple(wavelet, l_top, l_bot, tile);
+    const auto key = std::make_tuple(wavelet, l_top, l_bot, tw, th);
     auto it = cache.find(key);
     if (it == cache.end()) {
         int af, pf;
-        smem_needs(wavelet, l_top, l_bot, tile, &af, &pf);
+        smem_needs(wavelet, l_top, l_bot, tw, th, &af, &pf);
         it = cache.emplace(key, std::make_pair(af, pf)).first;
     }
     *a_floats = it->second.first;
@@ -911,7 +895,7 @@ void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_float
 
 // Shared-memory sizes and the folded 9/7 scales of a pass.
 void fill_tile_scales(TileArgs &a) {
-    smem_needs_cached(a.g.wavelet, a.l_top, a.l_bot, a.tile, &a.a_floats, &a.p_floats);
+    smem_needs_cached(a.g.wavelet, a.l_top, a.l_bot, a.tw, a.th, &a.a_floats, &a.p_floats);
     const double k2 = kK * kK;
     for (int l = 0; l <= kMaxLevels; ++l) {
         if (a.g.wavelet == WV_WAVELET_97) {
@@ -1023,7 +1007,7 @@ TileArgs base_args(const Geom &g, const int16_t *payload, const int32_t *table, 
 
 int decode_tiles_smem_bytes(const Geom &g) {
     int af, pf;
-    smem_needs(g.wavelet, g.levels, 1, g.tile, &af, &pf);
+    smem_needs(g.wavelet, g.levels, 1, g.tw, g.th, &af, &pf);
     return (af + pf) * 4;
 }
 
@@ -1043,7 +1027,8 @@ cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = g.levels;
     a.l_bot = 1;
-    a.tile = g.tile;
+    a.tw = g.tw;
+    a.th = g.th;
     for (int p = 0; p < 3; ++p) a.out_u8[p] = out_u8[p];
     a.out_f32 = out_f32;
     a.f32_plane = f32_plane;
@@ -1060,7 +1045,7 @@ cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const in
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = g.levels;
     a.l_bot = 3;
-    a.tile = g.ctile;
+    a.tw = a.th = g.ctile;
     for (int p = 0; p < 3; ++p) {
         a.ll_out[p] = ll2[p];
         a.ll_out_pitch[p] = ll2_pitch[p];
@@ -1079,7 +1064,8 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
     TileArgs a = base_args(g, payload, table, bands, err);
     a.l_top = 2;
     a.l_bot = 1;
-    a.tile = g.tile;
+    a.tw = g.tw;
+    a.th = g.th;
     for (int p = 0; p < 3; ++p) {
         a.ll_in[p] = ll2[p];
         a.ll_in_pitch[p] = ll2_pitch[p];

@@ -11,7 +11,8 @@
 //   tile_gen  uint32 [tiles]            generation that last selected a tile
 //   ctile_gen uint32 [coarse tiles]      generation that last listed a coarse tile
 //   ctiles    uint32 [coarse tiles]      coarse tiles the selected tiles need
-//   counters  int32 [16]                 [0] = tile count, [1] = coarse tile count
+//   counters  int32 [16]                 [0] = tile count, [1] = coarse tile count,
+//                                        [2] = strip tiles taken (strip kernel)
 //   err       int32                      first device-side error code
 #pragma once
 
@@ -31,6 +32,11 @@ constexpr int kLogCell = 5;
 constexpr int kTile = 128;      // default output tile side (plane pixels)
 constexpr int kThreads = 256;   // threads of the tile-decode CTA
 constexpr int kCoarseTile = 64; // default coarse tile side at level 2 (256 plane pixels)
+constexpr int kStripW = 224;    // output columns of a strip tile (one warp: 28 lanes x 8)
+#ifndef WV_STRIP_H
+#define WV_STRIP_H 64
+#endif
+constexpr int kStripH = WV_STRIP_H;   // default output rows of a strip tile
 
 // Subband index inside a level: 0 = LL (level L only), 1 = HL, 2 = LH, 3 = HH.
 struct PlaneGeom {
@@ -38,11 +44,10 @@ struct PlaneGeom {
     int nbx[kMaxLevels + 1];           // blocks per row of a level-l subband
     int nby[kMaxLevels + 1];
     int base[kMaxLevels + 1][4];       // first block id of (level, subband)
-    int tiles_x, tiles_y;
+    int tiles_x, tiles_y;              // output tiles (Geom::tw x Geom::th samples)
     int ctiles_x, ctiles_y;            // coarse tiles (Geom::ctile samples of LL_2)
     int sub;                           // luma pixels per plane pixel (1 or 2)
     int ll2_pitch;                     // floats per row of the LL_2 plane
-    int tile_shift;                    // log2 of the mask cells per tile side
 };
 
 struct Geom {
@@ -55,8 +60,13 @@ struct Geom {
     int cells_x, cells_y;
     int total_tiles;
     int total_ctiles;
-    int tile;    // output tile side (plane pixels): 64 or 128
+    int tw, th;  // output tile width and height (plane pixels): square 64 or 128, or a strip kStripW x th
+    int strip;   // 1: output tiles are strips decoded by the strip kernel (strip.cu)
     int ctile;   // coarse tile side (LL_2 samples): 32 or 64
+    // LL_2 window an output tile (tx, ty) reads: columns (tw / 4) tx + wx0 ..
+    // (tw / 4) tx + wx1, rows (th / 4) ty + wy0 .. (th / 4) ty + wy1 (before
+    // symmetric extension); the coarse tiles holding it are decoded first
+    int wx0, wx1, wy0, wy1;
 };
 
 // Coefficient frames that rebuild one frame (inverse inter-frame Haar):
@@ -109,7 +119,7 @@ struct TileArgs {
     const int32_t *table;
     Bands bands;
     int l_top, l_bot;        // levels synthesised: l_top down to l_bot
-    int tile;                // output tile side at level l_bot - 1
+    int tw, th;              // output tile width and height at level l_bot - 1
     const float *ll_in[3];   // LL_{l_top} planes when l_top < levels
     int ll_in_pitch[3];
     uint8_t *out_u8[3];      // l_bot == 1: samples
@@ -120,6 +130,7 @@ struct TileArgs {
     const uint8_t *fmask;    // foveation bits per mask cell (bit l-1: keep level l), or null
     const uint32_t *tiles;   // tile list (count entries)
     const int *count;
+    int *work;               // strip kernel: next tile to take (zeroed before the launch)
     int *err;
     int a_floats, p_floats;
     // 9/7: half the dequantisation step times the synthesis band scaling
@@ -213,6 +224,10 @@ cudaError_t paper_transcode(const void *bytes, size_t n, const PaperInfo &info, 
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h,
                   int eye = 0);
 int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
+// Strip geometry (output tiles kStripW x th, th a multiple of 32 in [32, 256])
+// for streams the strip kernel decodes (strip_eligible), else WV_ERR_ARG.
+int build_geom_strip(const wv_stream_desc &d, Geom *g, int th = kStripH, int ctile = kCoarseTile);
+bool strip_eligible(const wv_stream_desc &d, uint64_t n_payload);
 Bands frame_bands(const Geom &g, int frame);
 View make_view(float yaw, float pitch, float fov, int out_w, int out_h, int eq_w, int eq_h, int row0 = 0);
 int eye_view(const Geom &g, int eye, int *row0, int *rows);   // WV_ERR_ARG for an invalid eye
@@ -237,6 +252,10 @@ cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int
 cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, float *const *ll2, const int *ll2_pitch,
                                  const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
+cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const int32_t *table,
+                                 const Bands &bands, const float *const *ll2, const int *ll2_pitch,
+                                 uint8_t *const *out_u8, float *out_f32, int f32_plane,
+                                 const uint32_t *tiles, int *counters, int *err, cudaStream_t cs);
 cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
                                const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                uint8_t *const *out_u8, float *out_f32, int f32_plane,
@@ -245,7 +264,7 @@ void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const 
                      uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane = nullptr,
                      uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr);
 void fill_tile_scales(TileArgs &a);
-void smem_needs_cached(int wavelet, int l_top, int l_bot, int tile, int *a_floats, int *p_floats);
+void smem_needs_cached(int wavelet, int l_top, int l_bot, int tw, int th, int *a_floats, int *p_floats);
 
 // batched kernels
 void launch_footprint_batch(const RequestJob *reqs, const SurfaceJob *surfs, int n, int max_cx,
@@ -274,7 +293,10 @@ int encode_paper(const Geom &g, const void *const *planes, void *scratch, size_t
 }  // namespace wv
 
 struct wv_stream {
+    // g: geometry of the default decode (strip tiles when strip_eligible,
+    // else square tiles); gsq: square 128-sample tiles (decode modes 1, 2)
     wv::Geom g;
+    wv::Geom gsq;
     wv_stream_desc desc;
     int device = 0;
     cudaStream_t cs = nullptr;
@@ -292,7 +314,8 @@ struct wv_stream {
     uint32_t gen = 0;   // viewport generation (stamps in tile_gen / ctile_gen)
     float *ll2[3] = {nullptr, nullptr, nullptr};
     int ll2_pitch[3] = {0, 0, 0};
-    int decode_mode = 0;   // 0: coarse pass + fine pass (levels >= 3), 1: all levels fused
+    int decode_mode = 0;   // 0: default (strip fine pass), 1: all levels fused per square tile,
+                           // 2: coarse pass + square-tile fine pass
     int *counters = nullptr;
     int *err = nullptr;
     // A second set of per-viewport buffers (tile lists, counters, LL_2
