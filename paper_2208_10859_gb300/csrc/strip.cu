@@ -375,6 +375,52 @@ struct VState<0> {
     }
 };
 
+// Running vertical synthesis of N columns.  9/7: adjacent columns run as
+// pairs in packed fp32x2 arithmetic (each element rounds exactly as fmaf).
+template <int WAV, int N>
+struct VCols {
+    VState<WAV> s[N];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int c = 0; c < N; ++c) s[c].clear();
+    }
+    __device__ __forceinline__ void step(const int (&e)[N], const int (&o)[N], int (&oe)[N], int (&oo)[N]) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) s[c].step(e[c], o[c], oe[c], oo[c]);
+    }
+};
+template <int N>
+struct VCols<1, N> {
+    float2 po[N / 2], y1[N / 2], y2[N / 2], y3[N / 2];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) po[c] = y1[c] = y2[c] = y3[c] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void step(const float (&e)[N], const float (&o)[N], float (&oe)[N],
+                                         float (&oo)[N]) {
+        const float2 nd = make_float2(-kDelta, -kDelta), ng = make_float2(-kGamma, -kGamma);
+        const float2 nb = make_float2(-kBeta, -kBeta), na = make_float2(-kAlpha, -kAlpha);
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const float2 ee = make_float2(e[2 * c], e[2 * c + 1]);
+            const float2 o2 = make_float2(o[2 * c], o[2 * c + 1]);
+            const float2 y1k = __ffma2_rn(nd, __fadd2_rn(po[c], o2), ee);       // even row i
+            const float2 y2m = __ffma2_rn(ng, __fadd2_rn(y1[c], y1k), po[c]);   // odd row i - 1
+            const float2 y3m = __ffma2_rn(nb, __fadd2_rn(y2[c], y2m), y1[c]);   // even row i - 2
+            const float2 o4 = __ffma2_rn(na, __fadd2_rn(y3[c], y3m), y2[c]);    // odd row i - 3
+            oe[2 * c] = y3[c].x;                                                 // even row i - 4
+            oe[2 * c + 1] = y3[c].y;
+            oo[2 * c] = o4.x;
+            oo[2 * c + 1] = o4.y;
+            y3[c] = y3m;
+            y2[c] = y2m;
+            y1[c] = y1k;
+            po[c] = o2;
+        }
+    }
+};
+
+
 // Symmetric extension across the warp: a lane whose N interleaved columns
 // c0 .. c0 + N - 1 lie outside the line (active) takes each value from the
 // lane holding its mirror image -c (left side) or 2 Wl - 2 - c (right side);
@@ -493,11 +539,10 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
         r2[k].by = -1;
         r1[k].by = -1;
     }
-    VState<WAV> v2[4], v1[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v2[k].clear();
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v1[k].clear();
+    VCols<WAV, 4> v2;
+    VCols<WAV, 8> v1;
+    v2.clear();
+    v1.clear();
 
     const int n_l1 = TH / 2 + 4;                 // level-1 row pairs (TH a multiple of 4)
     const int P2 = P0 + n_l1 / 2;                // level-2 row pairs
@@ -585,13 +630,13 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
             hsynth<WAV, 4>(ev);
             hsynth<WAV, 4>(od);
             // LL_1 rows sig - D (even) and sig - D + 1 (odd) into the ring
+            T oe[4], oo[4];
+            v2.step(ev, od, oe, oo);
             float re[4], ro[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                T oe, oo;
-                v2[c].step(ev[c], od[c], oe, oo);
-                re[c] = to_f<T>(oe);
-                ro[c] = to_f<T>(oo);
+                re[c] = to_f<T>(oe[c]);
+                ro[c] = to_f<T>(oo[c]);
             }
             const int k0 = sig - D;
             *reinterpret_cast<float4 *>(ring + (k0 & (kRing - 1)) * kRingW + 4 * lane) =
@@ -654,8 +699,7 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                 hsynth<WAV, 8>(ev);
                 hsynth<WAV, 8>(od);
                 T oe[8], oo[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v1[c].step(ev[c], od[c], oe[c], oo[c]);
+                v1.step(ev, od, oe, oo);
                 const int r0 = rho - D;   // output rows r0 (even) and r0 + 1
                 if (writer && r0 >= Y0 && r0 < Y0 + TH) {
 #pragma unroll
