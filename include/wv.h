@@ -454,26 +454,29 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
  * allocate GPU memory themselves -- for example a plug-in whose host
  * application owns every device allocation -- but already hold a stream's
  * block table (int32 [num_frames][blocks per frame], the stream's table) and
- * coefficient payload (int16 blocks) in device memory they own.
+ * coefficient payload (int16 blocks, payload_blocks of them) in device
+ * memory they own.
  * desc describes the stream (host memory).  out_dev receives the plane's
  * width x height samples, row-major and tightly packed: uint8 (as_float = 0)
  * or float32 before rounding (as_float = 1), as in wv_decode_full.  Work is
- * enqueued on cuda_stream (NULL = legacy default stream) and the call returns
- * before it finishes.
+ * enqueued on cuda_stream (NULL = legacy default stream).  status == NULL:
+ * the call returns before the work finishes; otherwise it waits for it and
+ * stores the device error word in *status (host memory): WV_OK, or
+ * WV_ERR_FORMAT when a table entry was at or above payload_blocks (such an
+ * entry reads as an all-zero block, never outside the payload).
  * Scratch: the tile list and counters live in one static device array of
  * 16 KB + 256 bytes that every GPU loading the library holds until the
  * process exits; planes of more than 4096 tiles of 128 x 128 samples (larger
  * than 8192 x 8192) are rejected with WV_ERR_RANGE.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress, with
  * the device current); make that first call before any stream capture.
- * All calls share the array: calls whose work overlaps on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * Table entries must lie in [-1, number of payload blocks); they are not
- * checked on the device.  Calls no cudaMalloc, cudaFree or other allocating
- * routine. */
+ * All calls share the array (the error word included): calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Returns WV_ERR_ARG for payload_blocks == 0.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
 int wv_decode_plane_static(const wv_stream_desc *desc, const void *payload_dev,
-                           const void *table_dev, int frame, int plane, void *out_dev,
-                           int as_float, void *cuda_stream);
+                           size_t payload_blocks, const void *table_dev, int frame, int plane,
+                           void *out_dev, int as_float, void *cuda_stream, int *status);
 
 /* Wait for the stream's CUDA stream and read the device error word: WV_OK,
  * or the first error a kernel recorded since the previous call (the word is
@@ -517,6 +520,13 @@ int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host,
  * in a cell without the bit. */
 int wv_cone_bytes_fovea(wv_stream *s, int frame, const uint8_t *mask_host,
                         const uint8_t *fovea_host, unsigned long long *bytes);
+
+/* wv_cone_bytes split by the pass that reads the coefficients: *fine =
+ * levels 1 and 2 (the fine pass; for streams of one or two levels the LL
+ * band too), *coarse = levels 3 and above with the LL band (the coarse
+ * pass).  Host computation. */
+int wv_cone_bytes_split(wv_stream *s, int frame, const uint8_t *mask_host, unsigned long long *fine,
+                        unsigned long long *coarse);
 
 /* Algorithmic bytes of one request: runs the request's footprint on the
  * stream's CUDA stream (synchronising it), then on the host the coefficient

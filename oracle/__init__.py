@@ -67,15 +67,25 @@ WAVELET_97 = 1
 # --------------------------------------------------------------------------
 
 def build() -> str:
-    """Compile wv_oracle.c with gcc into oracle/_build/liboracle.so."""
+    """Compile wv_oracle.c with gcc into oracle/_build/liboracle.so (with
+    OpenMP where the compiler has it, else single-threaded)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not os.path.exists(_LIB_PATH)
             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:5] + ["-fopenmp"] + base[5:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def set_threads(n: int) -> int:
+    """Host threads the 2D transforms use (n <= 0 keeps the current count);
+    returns the count in effect (1 without OpenMP)."""
+    return int(_load().or_set_threads(int(n)))
 
 
 def _load():
@@ -95,6 +105,8 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = [p, L, L, ctypes.c_int]
             f.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 

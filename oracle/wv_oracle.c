@@ -1,9 +1,10 @@
 /*
  * wv_oracle.c -- TEST INFRASTRUCTURE, not part of the decoder library.
  *
- * Plain, slow, single-threaded reference lifting transforms used only by the
- * tests, the smoke check and the benchmark's CPU-baseline leg.  Shares no code
- * with the CUDA library.
+ * Plain, slow reference lifting transforms used only by the tests, the smoke
+ * check and the benchmark's CPU-baseline leg (the lines of a 2D level may be
+ * shared out among host threads with OpenMP; the arithmetic of a line is the
+ * same).  Shares no code with the CUDA library.
  *
  * Method (Groth et al., "Wavelet-Based Fast Decoding of 360 deg Videos"):
  *   Sec. 3.1, Eq. 1: frame-wise 2D fast wavelet transform, l levels, with the
@@ -25,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static const double ALPHA = -1.586134342059924;
 static const double BETA = -0.052980118572961;
@@ -143,96 +147,137 @@ void or_inv53_1d(const int64_t *in, int64_t *out, long n)
     free(y);
 }
 
-/* ---- 2D multi-level transforms on a w x h row-major image, in place ---- */
+/* ---- 2D multi-level transforms on a w x h row-major image, in place ----
+ *
+ * The rows (columns) of one level are independent lines; with OpenMP they are
+ * shared out among the host's threads (or_set_threads), each thread using its
+ * own line buffers.  The arithmetic per line is the same either way. */
+
+static int thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+static int thread_count(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Threads the 2D transforms use (1 when built without OpenMP). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return thread_count();
+}
 
 int or_fwd2d_97(double *img, long w, long h, int levels)
 {
     long m = (w > h ? w : h);
-    double *a = malloc((size_t)m * sizeof(double));
-    double *b = malloc((size_t)m * sizeof(double));
-    double *y = malloc((size_t)m * sizeof(double));
-    if (!a || !b || !y) { free(a); free(b); free(y); return -1; }
+    double *s = malloc((size_t)thread_count() * 3 * (size_t)m * sizeof(double));
+    if (!s) return -1;
     for (int l = 0; l < levels; ++l) {
         long cw = w >> l, ch = h >> l;
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < cw; ++c) {           /* vertical analysis */
+            double *a = s + (size_t)thread_id() * 3 * m, *b = a + m, *y = b + m;
             for (long r = 0; r < ch; ++r) a[r] = img[r * w + c];
             fwd97_line(a, b, ch, y);
             for (long r = 0; r < ch; ++r) img[r * w + c] = b[r];
         }
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < ch; ++r) {           /* horizontal analysis */
+            double *b = s + (size_t)thread_id() * 3 * m, *y = b + m;
             fwd97_line(img + r * w, b, cw, y);
             memcpy(img + r * w, b, (size_t)cw * sizeof(double));
         }
     }
-    free(a); free(b); free(y);
+    free(s);
     return 0;
 }
 
 int or_inv2d_97(double *img, long w, long h, int levels)
 {
     long m = (w > h ? w : h);
-    double *a = malloc((size_t)m * sizeof(double));
-    double *b = malloc((size_t)m * sizeof(double));
-    double *y = malloc((size_t)m * sizeof(double));
-    if (!a || !b || !y) { free(a); free(b); free(y); return -1; }
+    double *s = malloc((size_t)thread_count() * 3 * (size_t)m * sizeof(double));
+    if (!s) return -1;
     for (int l = levels - 1; l >= 0; --l) {
         long cw = w >> l, ch = h >> l;
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < ch; ++r) {           /* horizontal synthesis */
+            double *b = s + (size_t)thread_id() * 3 * m, *y = b + m;
             inv97_line(img + r * w, b, cw, y);
             memcpy(img + r * w, b, (size_t)cw * sizeof(double));
         }
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < cw; ++c) {           /* vertical synthesis */
+            double *a = s + (size_t)thread_id() * 3 * m, *b = a + m, *y = b + m;
             for (long r = 0; r < ch; ++r) a[r] = img[r * w + c];
             inv97_line(a, b, ch, y);
             for (long r = 0; r < ch; ++r) img[r * w + c] = b[r];
         }
     }
-    free(a); free(b); free(y);
+    free(s);
     return 0;
 }
 
 int or_fwd2d_53(int64_t *img, long w, long h, int levels)
 {
     long m = (w > h ? w : h);
-    int64_t *a = malloc((size_t)m * sizeof(int64_t));
-    int64_t *b = malloc((size_t)m * sizeof(int64_t));
-    int64_t *y = malloc((size_t)m * sizeof(int64_t));
-    if (!a || !b || !y) { free(a); free(b); free(y); return -1; }
+    int64_t *s = malloc((size_t)thread_count() * 3 * (size_t)m * sizeof(int64_t));
+    if (!s) return -1;
     for (int l = 0; l < levels; ++l) {
         long cw = w >> l, ch = h >> l;
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < cw; ++c) {
+            int64_t *a = s + (size_t)thread_id() * 3 * m, *b = a + m, *y = b + m;
             for (long r = 0; r < ch; ++r) a[r] = img[r * w + c];
             fwd53_line(a, b, ch, y);
             for (long r = 0; r < ch; ++r) img[r * w + c] = b[r];
         }
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < ch; ++r) {
+            int64_t *b = s + (size_t)thread_id() * 3 * m, *y = b + m;
             fwd53_line(img + r * w, b, cw, y);
             memcpy(img + r * w, b, (size_t)cw * sizeof(int64_t));
         }
     }
-    free(a); free(b); free(y);
+    free(s);
     return 0;
 }
 
 int or_inv2d_53(int64_t *img, long w, long h, int levels)
 {
     long m = (w > h ? w : h);
-    int64_t *a = malloc((size_t)m * sizeof(int64_t));
-    int64_t *b = malloc((size_t)m * sizeof(int64_t));
-    int64_t *y = malloc((size_t)m * sizeof(int64_t));
-    if (!a || !b || !y) { free(a); free(b); free(y); return -1; }
+    int64_t *s = malloc((size_t)thread_count() * 3 * (size_t)m * sizeof(int64_t));
+    if (!s) return -1;
     for (int l = levels - 1; l >= 0; --l) {
         long cw = w >> l, ch = h >> l;
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < ch; ++r) {
+            int64_t *b = s + (size_t)thread_id() * 3 * m, *y = b + m;
             inv53_line(img + r * w, b, cw, y);
             memcpy(img + r * w, b, (size_t)cw * sizeof(int64_t));
         }
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < cw; ++c) {
+            int64_t *a = s + (size_t)thread_id() * 3 * m, *b = a + m, *y = b + m;
             for (long r = 0; r < ch; ++r) a[r] = img[r * w + c];
             inv53_line(a, b, ch, y);
             for (long r = 0; r < ch; ++r) img[r * w + c] = b[r];
         }
     }
-    free(a); free(b); free(y);
+    free(s);
     return 0;
 }

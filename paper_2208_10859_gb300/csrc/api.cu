@@ -378,10 +378,10 @@ void dilate_axis(const std::vector<uint8_t> &in, std::vector<uint8_t> &out, int 
 // fbits: optional foveation bits per mask cell (bit l - 1 keeps the details
 // of level l = 1, 2); dropped coefficients are not read.
 unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask,
-                              const uint8_t *fbits = nullptr) {
+                              const uint8_t *fbits = nullptr, unsigned long long *fine_part = nullptr) {
     const Geom &g = s->g;
     const Bands b = frame_bands(g, frame);
-    unsigned long long total = 0;
+    unsigned long long total = 0, fine = 0;
     for (int p = 0; p < g.planes; ++p) {
         const PlaneGeom &pg = g.p[p];
         int w = pg.w, h = pg.h;
@@ -397,7 +397,10 @@ unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask
             }
             const int bid = pg.base[level][sub] + (ky >> g.log2b) * pg.nbx[level] + (kx >> g.log2b);
             for (int k = 0; k < b.n; ++k)
-                if (s->table_host[(size_t)b.t[k] * g.nbpf + bid] >= 0) total += 2;
+                if (s->table_host[(size_t)b.t[k] * g.nbpf + bid] >= 0) {
+                    total += 2;
+                    if (level <= 2 && (sub != 0 || level < g.levels || g.levels <= 2)) fine += 2;
+                }
         };
         for (int l = 1; l <= g.levels; ++l) {
             dilate_axis(R, tmp, w, h, true, g.wavelet);
@@ -418,6 +421,7 @@ unsigned long long cone_bytes(const wv_stream *s, int frame, const uint8_t *mask
             for (int x = 0; x < w; ++x)
                 if (R[(size_t)y * w + x]) count(g.levels, 0, x, y);
     }
+    if (fine_part) *fine_part = fine;
     return total;
 }
 
@@ -909,6 +913,14 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
 int wv_cone_bytes(wv_stream *s, int frame, const uint8_t *mask_host, unsigned long long *bytes) {
     if (!s || !mask_host || !bytes || frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
     *bytes = cone_bytes(s, frame, mask_host);
+    return WV_OK;
+}
+
+int wv_cone_bytes_split(wv_stream *s, int frame, const uint8_t *mask_host, unsigned long long *fine,
+                        unsigned long long *coarse) {
+    if (!s || !mask_host || !fine || !coarse || frame < 0 || frame >= s->g.num_frames) return WV_ERR_ARG;
+    const unsigned long long total = cone_bytes(s, frame, mask_host, nullptr, fine);
+    *coarse = total - *fine;
     return WV_OK;
 }
 

@@ -240,7 +240,11 @@ __device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, cons
     bool have[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+        int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+        if (a.n_slots > 0 && slot >= a.n_slots) {   // bad table entry: absent, recorded
+            record_error(a.err, WV_ERR_FORMAT);
+            slot = -1;
+        }
         have[b] = slot >= 0;
         const int v = have[b] ? (int)__ldg(&a.payload[(size_t)slot * bsz + off]) : 0;
         q[b] = make_uint4((uint32_t)(uint16_t)v, 0, 0, 0);
@@ -303,7 +307,11 @@ __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg
         const size_t off = (size_t)((t.ky & bm) << lb) + (kx & bm);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+            int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+            if (a.n_slots > 0 && slot >= a.n_slots) {   // bad table entry: absent, recorded
+                record_error(a.err, WV_ERR_FORMAT);
+                slot = -1;
+            }
             if (slot >= 0 && any) {
                 r.have[e][b] = true;
                 r.q[e][b] = __ldg(reinterpret_cast<const uint4 *>(a.payload + (size_t)slot * bsz + off));
@@ -1023,8 +1031,9 @@ int decode_tiles_grid(const Geom &g) {
 cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int32_t *table,
                                 const Bands &bands, uint8_t *const *out_u8, float *out_f32,
                                 int f32_plane, const uint32_t *tiles, const int *counters,
-                                int *err, cudaStream_t cs) {
+                                int *err, cudaStream_t cs, int n_slots) {
     TileArgs a = base_args(g, payload, table, bands, err);
+    a.n_slots = n_slots;
     a.l_top = g.levels;
     a.l_bot = 1;
     a.tw = g.tw;

@@ -7,6 +7,8 @@
 // wv_decode_plane_static serves them: its only scratch, the tile list and
 // counters of the tile-decode kernel, lives in the file-scope array below,
 // which every GPU that loads the library holds until the process exits.
+#include <stdint.h>
+
 #include <mutex>
 
 #include "wv_impl.h"
@@ -48,9 +50,10 @@ int scratch_address(void **out) {
 }  // namespace
 
 extern "C" int wv_decode_plane_static(const wv_stream_desc *desc, const void *payload_dev,
-                                      const void *table_dev, int frame, int plane, void *out_dev,
-                                      int as_float, void *cuda_stream) {
+                                      size_t payload_blocks, const void *table_dev, int frame, int plane,
+                                      void *out_dev, int as_float, void *cuda_stream, int *status) {
     if (!desc || !payload_dev || !table_dev || !out_dev) return WV_ERR_ARG;
+    if (payload_blocks == 0 || payload_blocks > (size_t)INT32_MAX) return WV_ERR_ARG;
     if (desc->quant != 0) return WV_ERR_ARG;   // the byte quantiser needs per-frame parameters
     wv::Geom g;
     if (wv::build_geom(*desc, &g) != WV_OK) return WV_ERR_ARG;
@@ -74,9 +77,20 @@ extern "C" int wv_decode_plane_static(const wv_stream_desc *desc, const void *pa
     if (as_float) f32 = (float *)out_dev;
     else outs[plane] = (uint8_t *)out_dev;
     wv::launch_all_tiles(g, plane, tiles, counters, cs);
-    const cudaError_t e = wv::launch_decode_tiles(
+    // table entries at or above payload_blocks read as absent blocks and
+    // leave WV_ERR_FORMAT in the error word
+    cudaError_t e = wv::launch_decode_tiles(
         g, (const int16_t *)payload_dev, (const int32_t *)table_dev, wv::frame_bands(g, frame), outs,
-        f32, as_float ? plane : -1, tiles, counters, err, cs);
+        f32, as_float ? plane : -1, tiles, counters, err, cs, (int)payload_blocks);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return WV_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? WV_OK : WV_ERR_CUDA;
+    if (status) {
+        // wait for this call's work and hand back the device error word
+        if (cudaMemcpyAsync(status, err, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+            cudaStreamSynchronize(cs) != cudaSuccess) {
+            cudaGetLastError();
+            return WV_ERR_CUDA;
+        }
+    }
+    return WV_OK;
 }

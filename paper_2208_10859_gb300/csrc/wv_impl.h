@@ -132,6 +132,10 @@ struct TileArgs {
     const int *count;
     int *work;               // strip kernel: next tile to take (zeroed before the launch)
     int *err;
+    // payload blocks held (0: not checked; streams validate their table when
+    // opened): a table entry at or above it reads as an absent block and
+    // records WV_ERR_FORMAT
+    int n_slots;
     int a_floats, p_floats;
     // 9/7: half the dequantisation step times the synthesis band scaling
     // folded over all levels.  Synthesis scales a low band by K and a high
@@ -248,7 +252,7 @@ int decode_tiles_grid(const Geom &g);
 cudaError_t launch_decode_tiles(const Geom &g, const int16_t *payload, const int32_t *table,
                                 const Bands &bands, uint8_t *const *out_u8, float *out_f32,
                                 int f32_plane, const uint32_t *tiles, const int *counters,
-                                int *err, cudaStream_t cs);
+                                int *err, cudaStream_t cs, int n_slots = 0);
 cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, float *const *ll2, const int *ll2_pitch,
                                  const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);

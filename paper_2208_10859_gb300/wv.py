@@ -119,8 +119,8 @@ def _lib():
             "wv_encode_sizes": (c_int, [ctypes.POINTER(StreamDesc), ctypes.POINTER(c_size), ctypes.POINTER(c_size)]),
             "wv_encode": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, vp, c_size,
                                   ctypes.POINTER(c_size), vp]),
-            "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_int, c_int, vp,
-                                               c_int, vp]),
+            "wv_decode_plane_static": (c_int, [ctypes.POINTER(StreamDesc), vp, c_size, vp, c_int, c_int, vp,
+                                               c_int, vp, ctypes.POINTER(c_int)]),
             "wv_release_default_batch": (None, []),
             "wv_encode_paper": (c_int, [ctypes.POINTER(StreamDesc), vp, vp, c_size, fl, fl, vp, c_size,
                                         ctypes.POINTER(c_size), vp]),
@@ -145,6 +145,8 @@ def _lib():
             "wv_server_reset_stats": (c_int, [vp]),
             "wv_server_close": (None, [vp]),
             "wv_cone_bytes_fovea": (c_int, [vp, c_int, vp, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+            "wv_cone_bytes_split": (c_int, [vp, c_int, vp, ctypes.POINTER(ctypes.c_ulonglong),
+                                            ctypes.POINTER(ctypes.c_ulonglong)]),
             "wv_request_bytes": (c_int, [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_ulonglong),
                                          ctypes.POINTER(ctypes.c_ulonglong)]),
             "wv_batch_create": (c_int, [vp, ctypes.POINTER(vp)]),
@@ -180,7 +182,7 @@ def exported_symbols() -> list[str]:
             "wv_cone_bytes", "wv_profile_begin", "wv_profile_end", "wv_launches_per_viewport",
             "wv_set_decode_mode",
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
-            "wv_cone_bytes_fovea", "wv_request_bytes", "wv_encode_paper",
+            "wv_cone_bytes_fovea", "wv_cone_bytes_split", "wv_request_bytes", "wv_encode_paper",
             "wv_cnn_param_count", "wv_cnn_create", "wv_cnn_close", "wv_cnn_get_params", "wv_cnn_set_params",
             "wv_cnn_forward", "wv_cnn_gradients", "wv_cnn_train_step", "wv_cnn_sync_status",
             "wv_decode_viewport_filtered",
@@ -291,6 +293,15 @@ class Stream:
             raise ValueError("uv must be a contiguous CUDA float32 tensor of shape (H, W, 2)")
         _check(_lib().wv_resample_at(self._handle, ctypes.c_void_p(uv.data_ptr()), ctypes.byref(img)),
                "wv_resample_at")
+
+    def cone_bytes_split(self, frame: int, mask: np.ndarray) -> tuple[int, int]:
+        """Coefficient cone bytes read by the fine pass (levels 1-2) and by the
+        coarse pass (levels 3 and above)."""
+        m = np.ascontiguousarray(mask, np.uint8)
+        fine, coarse = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        _check(_lib().wv_cone_bytes_split(self._handle, frame, m.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(fine), ctypes.byref(coarse)), "wv_cone_bytes_split")
+        return int(fine.value), int(coarse.value)
 
     def cone_bytes(self, frame: int, mask: np.ndarray, fovea: np.ndarray | None = None) -> int:
         m = np.ascontiguousarray(mask, np.uint8)

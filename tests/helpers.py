@@ -109,6 +109,15 @@ def tol_97_levels() -> float:
     return 1e-4 * 255.0
 
 
+def reg_97_levels() -> float:
+    """Regression bound on |float32 decode - fp64 oracle| for 9/7 samples in
+    8-bit levels, about twice the largest difference measured on the test
+    workloads and the 8192^2 benchmark frames: a change in the order or
+    precision of the float32 lifting that loses a bit shows here long before
+    it reaches the 1e-4 full-scale bound."""
+    return 5.0e-4
+
+
 def near_half(x: np.ndarray, eps: float = 2e-3) -> np.ndarray:
     """Samples whose exact value is within eps of a rounding boundary k + 1/2
     (where float32 and fp64 may round to different 8-bit values)."""
@@ -152,6 +161,46 @@ def quanta(t: np.ndarray, eps, k: int = 4):
     hi = np.floor((t + eps) * 256 + 0.5)
     qs = [np.minimum(lo + i, hi) / 256.0 for i in range(k)]
     return np.stack(qs, -1), (hi - lo + 1) > k
+
+
+def rgba_wide_check(planes, p: O.Params, u, v, eps_u, eps_v, got, eye: int = 0, kmax: int = 512):
+    """Per-pixel check for pixels whose float32 position bound spans more than
+    four quanta per axis (near a pole the longitude error grows as
+    1/cos(latitude)): the device value must equal the colour conversion of
+    some luma value the oracle's plane takes at a 1/256 position inside the
+    pixel's luma bound and some chroma pair it takes inside the chroma bound
+    (the two boxes taken independently: a superset of the positions the
+    device can produce).  Returns a status per pixel: 0 matched, 1 no match,
+    2 excused (more than kmax quanta per axis)."""
+    r0, nr = O.eye_rows(p, eye)
+    status = np.zeros(u.shape[0], np.int8)
+    for i in range(u.shape[0]):
+        lo_u, hi_u = np.floor((u[i] - eps_u[i]) * 256 + 0.5), np.floor((u[i] + eps_u[i]) * 256 + 0.5)
+        lo_v, hi_v = np.floor((v[i] - eps_v[i]) * 256 + 0.5), np.floor((v[i] + eps_v[i]) * 256 + 0.5)
+        if hi_u - lo_u + 1 > kmax or hi_v - lo_v + 1 > kmax:
+            status[i] = 2
+            continue
+        qu = np.arange(lo_u, hi_u + 1) / 256.0
+        qv = np.arange(lo_v, hi_v + 1) / 256.0
+        U, V = np.meshgrid(qu, qv)
+        ys = np.unique(O.bilinear(planes[0], U.ravel(), V.ravel(), (r0, nr)))
+        if p.planes == 3:
+            uc, vc = O.chroma_coords(u[i:i + 1], v[i:i + 1])
+            lo_c = np.floor((uc[0] - eps_u[i] / 2) * 256 + 0.5), np.floor((uc[0] + eps_u[i] / 2) * 256 + 0.5)
+            lo_d = np.floor((vc[0] - eps_v[i] / 2) * 256 + 0.5), np.floor((vc[0] + eps_v[i] / 2) * 256 + 0.5)
+            UC, VC = np.meshgrid(np.arange(lo_c[0], lo_c[1] + 1) / 256.0, np.arange(lo_d[0], lo_d[1] + 1) / 256.0)
+            cr_ = (r0 // 2, nr // 2)
+            cb = O.bilinear(planes[1], UC.ravel(), VC.ravel(), cr_)
+            cr = O.bilinear(planes[2], UC.ravel(), VC.ravel(), cr_)
+            cc = np.unique(np.stack([cb, cr], -1), axis=0)
+        else:
+            cc = np.array([[128, 128]])
+        Y = np.repeat(ys, cc.shape[0])
+        C = np.tile(cc, (ys.shape[0], 1))
+        cand = O.ycbcr_to_rgba(Y, C[:, 0], C[:, 1])
+        if not np.any(np.all(cand == got[i][None, :], axis=-1)):
+            status[i] = 1
+    return status
 
 
 def rgba_candidates(planes, p: O.Params, u, v, eps_u, eps_v, eye: int = 0):

@@ -40,6 +40,7 @@ def test_untranscoded_codes_decode_within_tolerance():
             torch.cuda.synchronize()
             err = np.abs(out.cpu().numpy().astype(np.float64) - ref_x)
             assert err.max() <= H.tol_97_levels(), (f, pl, err.max())
+            assert err.max() <= H.reg_97_levels(), (f, pl, err.max())
     assert s.sync_status() == 0
 
 

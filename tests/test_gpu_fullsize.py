@@ -45,7 +45,9 @@ def test_full_planes_within_tolerance(full):
         s.decode_full(1, pl, u8)
         torch.cuda.synchronize()
         err = np.abs(f.cpu().numpy().astype(np.float64) - ref_x)
+        print(f"plane {pl}: max |float32 - fp64| = {err.max():.3e} levels")
         assert err.max() <= H.tol_97_levels(), (pl, float(err.max()))
+        assert err.max() <= H.reg_97_levels(), (pl, float(err.max()))
         diff = u8.cpu().numpy() != ref_u8
         assert not np.any(diff & ~H.near_half(ref_x)), (pl, int(diff.sum()))
     assert s.sync_status() == 0
@@ -82,10 +84,19 @@ def test_full_size_viewports(full):
         cand2, _ = H.rgba_candidates(alt, p, u, v, eu, ev)
         ok |= np.any(np.all(cand2 == g[:, None, :], axis=-1), axis=-1)
         assert int(np.sum(~ok & ~flag)) == 0
-        # excused: pixels whose float32 position bound spans more than four
-        # quanta per axis -- near a pole in view the longitude error grows as
-        # 1 / cos(latitude) (11 % of the pixels for a view reaching 93 deg)
-        assert int(np.sum(flag)) <= 0.15 * idx.size
+        # pixels whose float32 position bound spans more than four quanta per
+        # axis (near a pole in view the longitude error grows as
+        # 1 / cos(latitude)): checked one by one over their whole bound, with
+        # either rounding of near-half samples
+        wide = np.nonzero(flag & ~ok)[0]
+        s1 = H.rgba_wide_check(planes, p, u[wide], v[wide], eu[wide], ev[wide], g[wide])
+        s2 = H.rgba_wide_check(alt, p, u[wide], v[wide], eu[wide], ev[wide], g[wide])
+        matched = (s1 == 0) | (s2 == 0)
+        excused = (s1 == 2) & ~matched
+        print(f"pose ({yaw:.2f}, {pitch:.2f}): {int(flag.sum())} wide-bound pixels, "
+              f"{int(excused.sum())} excused")
+        assert int(np.sum(~matched & ~excused)) == 0
+        assert int(excused.sum()) <= 0.01 * idx.size
     assert s.sync_status() == 0
 
 
