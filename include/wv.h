@@ -288,6 +288,19 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info);
  * independent wv_decode_viewport calls, scheduled as one batch). */
 int wv_batch_set_sharing(wv_batch *b, int on);
 
+/* Polls of the tile decode's bounded wait (a fine tile waiting for its
+ * target's coarse tiles) before it gives up, records WV_ERR_TIMEOUT in the
+ * batch's error word and decodes with what is there (all reads stay in
+ * bounds).  Default and maximum 2^21 (about half a second); polls = 0
+ * makes every such wait give up at once -- the failure path, exercised
+ * without a GPU fault.  Takes effect from the next wv_batch_decode. */
+int wv_batch_set_wait_limit(wv_batch *b, int polls);
+
+/* Test hook: the next n device allocations the library makes itself
+ * (wv_open_stream without caller memory, batch arenas) fail as if the device
+ * were out of memory; the calls then return WV_ERR_OOM.  n = 0 clears it. */
+void wv_debug_fail_device_allocs(int n);
+
 /* on = 1: run batches as direct launches with CUDA events between the steps
  * (wv_batch_stats reports per-step times); on = 0: CUDA graph (default). */
 int wv_batch_set_timing(wv_batch *b, int on);
@@ -414,6 +427,14 @@ void wv_cnn_close(wv_cnn *c);
 int wv_cnn_get_params(wv_cnn *c, float *params_host);
 /* Replace the parameters (and reset the optimiser state). */
 int wv_cnn_set_params(wv_cnn *c, const float *params_host);
+
+/* Optimiser state, for checkpointing and resuming training (no counterpart
+ * in the paper): the Adam first and second moments (host, wv_cnn_param_count()
+ * floats each, in the parameter layout) and the number of Adam steps taken
+ * (its bias correction).  get waits for the device; set must follow
+ * wv_cnn_set_params, which clears the state. */
+int wv_cnn_get_state(wv_cnn *c, float *m_host, float *v_host, int *steps);
+int wv_cnn_set_state(wv_cnn *c, const float *m_host, const float *v_host, int steps);
 
 /* y = network(x) for n images of h x w (device float planes). */
 int wv_cnn_forward(wv_cnn *c, const float *x_dev, float *y_dev, int n, int h, int w, void *cuda_stream);

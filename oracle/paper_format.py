@@ -11,9 +11,10 @@ The paper's own coding of the wavelet coefficients, written step by step:
   T = alpha ((l_max - l) / l_max)^2 + H (Eq. 3), and after the inter-frame
   transform (Sec. 3.2, run to the last level) with the same form, the
   inter-frame constant and the temporal level; H(y) = 1 - sin(pi y / S_y)
-  (Sec. 3.6) with y the row inside the subband and S_y its height; the
-  approximation band takes l = l_max (threshold H only); a coefficient
-  survives when |W| > T;
+  (Sec. 3.6) with y the row inside the subband and S_y its height, added on
+  the detail bands only (the approximation band takes l = l_max, so its
+  threshold is 0; the temporal low band likewise); a coefficient survives
+  when |W| > T;
 * quantisation to one byte (Sec. 3.3): c_d = round((c - c_min) / (c_max -
   c_min) * 255) with the extremes of the surviving coefficients, separately
   for the approximation band and for all detail bands, per coefficient frame
@@ -66,25 +67,30 @@ def mapping_factor(rows: int) -> np.ndarray:
     return 1.0 - np.sin(math.pi * np.arange(rows) / rows)
 
 
-def threshold_map(w: int, h: int, levels: int, alpha: float, level_of=None) -> np.ndarray:
-    """Per-coefficient threshold of a Mallat plane (Eq. 3): subband level l
-    (LL: l_max), row y inside the subband.  level_of maps a spatial level to
-    the level used in the alpha term (default: itself)."""
+def threshold_map(w: int, h: int, levels: int, alpha: float) -> np.ndarray:
+    """Per-coefficient threshold of a Mallat plane (Eq. 3): a detail band of
+    level l takes alpha ((l_max - l) / l_max)^2 + H(y), y its row inside the
+    subband; the approximation band (l = l_max) takes the level term alone,
+    i.e. 0.  H (Sec. 3.6) thins the detail that the equirectangular mapping
+    oversamples toward the poles; applied to the approximation band it
+    would remove the image itself there."""
     T = np.zeros((h, w))
     for (name, lev, x0, y0, sw, sh) in subbands(w, h, levels):
         l = levels if name == "LL" else lev
         t = alpha * ((levels - l) / levels) ** 2
-        T[y0:y0 + sh, x0:x0 + sw] = t + mapping_factor(sh)[:, None]
+        T[y0:y0 + sh, x0:x0 + sw] = t if name == "LL" else t + mapping_factor(sh)[:, None]
     return T
 
 
 def temporal_threshold_map(w: int, h: int, levels: int, alpha_t: float, j: int, k: int) -> np.ndarray:
     """Inter-frame threshold of a coefficient frame of temporal level j (0 =
-    the low band, treated as level k): alpha_t ((k - j) / k)^2 + H(y)."""
+    the low band, treated as level k): alpha_t ((k - j) / k)^2, plus H(y) on
+    the spatial detail bands of the temporal detail frames (j >= 1)."""
     jj = k if j == 0 else j
     T = np.zeros((h, w))
     for (name, lev, x0, y0, sw, sh) in subbands(w, h, levels):
-        T[y0:y0 + sh, x0:x0 + sw] = alpha_t * ((k - jj) / k) ** 2 + mapping_factor(sh)[:, None]
+        t = alpha_t * ((k - jj) / k) ** 2
+        T[y0:y0 + sh, x0:x0 + sw] = t if (name == "LL" or j == 0) else t + mapping_factor(sh)[:, None]
     return T
 
 

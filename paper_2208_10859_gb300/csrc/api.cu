@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -160,6 +161,8 @@ Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
 }
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? WV_OK : WV_ERR_CUDA; }
+
+std::atomic<int> g_fail_allocs{0};   // device allocations still to fail (test hook)
 
 void prof_begin(wv_stream *s, int kind) {
     if (!s->prof) return;
@@ -455,6 +458,14 @@ void fovea_bits_host(const Geom &g, double yaw, double pitch, const wv_request &
 
 namespace wv {
 
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 namespace {
 
 // Common geometry of both tile organisations: output tiles tw x th (plane
@@ -737,7 +748,7 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
         }
         s->dmem = device_mem;
     } else {
-        if (cudaMalloc(&s->dmem, L.total) != cudaSuccess) {
+        if (dev_alloc(&s->dmem, L.total) != cudaSuccess) {
             cudaGetLastError();
             if (s->host_payload) cudaFreeHost(s->host_payload);
             delete s;
@@ -810,6 +821,8 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
     *out = s;
     return WV_OK;
 }
+
+void wv_debug_fail_device_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
 
 int wv_set_cuda_stream(wv_stream *s, void *cuda_stream) {
     if (!s) return WV_ERR_ARG;

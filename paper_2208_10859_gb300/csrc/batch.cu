@@ -49,6 +49,10 @@ struct Surface {
     size_t recon[3], ll2[3], fmask, stamp;
 };
 
+// Arena word holding the bounded wait's poll limit (inside the 256 bytes
+// before the job tables; the error word is at offset 0).
+constexpr size_t kWaitWord = 64;
+
 struct Plan {
     std::vector<Surface> surf;
     std::vector<int> req_surface;
@@ -86,6 +90,7 @@ struct wv_batch {
     bool timing = false;
     cudaEvent_t ev[5] = {};
     bool share = true;                 // unfoveated requests of one (stream, frame) share a surface
+    int wait_polls = kBatchWaitPolls;  // polls of the tile decode's bounded wait (arena word at kWaitWord)
 };
 
 namespace {
@@ -238,6 +243,7 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
     int *err = (int *)(base + P.err);
     SurfaceJob *sj = (SurfaceJob *)(b->host + P.jobs);
     RequestJob *rj = (RequestJob *)(b->host + P.reqs);
+    *(int *)(b->host + kWaitWord) = b->wait_polls;
     for (size_t i = 0; i < P.surf.size(); ++i) {
         const Surface &S = P.surf[i];
         SurfaceJob J;
@@ -290,7 +296,8 @@ cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool tim
     const RequestJob *rq = (const RequestJob *)(base + P.reqs);
     int *ctr = (int *)(base + P.ctr);
     const int m = (int)P.surf.size();
-    cudaError_t e = cudaMemcpyAsync(base + P.jobs, b->host + P.jobs, P.job_bytes - P.jobs,
+    // the wait limit word, then the job tables (the error word at 0 stays)
+    cudaError_t e = cudaMemcpyAsync(base + kWaitWord, b->host + kWaitWord, P.job_bytes - kWaitWord,
                                     cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return e;
     e = timed ? cudaEventRecord(b->staged, cs) : cudaEventRecordWithFlags(b->staged, cs, cudaEventRecordExternal);
@@ -313,7 +320,8 @@ cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool tim
         e = launch_decode_batch(group >= 4 ? WV_WAVELET_97 : group / 2, c % kMaxBands + 1, group % 2 == 1,
                                 group >= 4, surfs,
                                 lists.coarse[c], lists.fine[c], ctr + 4 * c,
-                                ctr + kBatchCtr, (int *)(base + P.err), P.smem[c], cs);
+                                ctr + kBatchCtr, (int *)(base + P.err), (const int *)(base + kWaitWord), P.smem[c],
+                                cs);
         if (e != cudaSuccess) return e;
     }
     if (timed) cudaEventRecord(b->ev[3], cs);
@@ -342,7 +350,7 @@ int ensure_memory(wv_batch *b, const Plan &P) {
         b->dmem = nullptr;
         b->dbytes = 0;
         const size_t want = P.total + P.total / 4;
-        if (cudaMalloc((void **)&b->dmem, want) != cudaSuccess) {
+        if (dev_alloc((void **)&b->dmem, want) != cudaSuccess) {
             cudaGetLastError();
             return WV_ERR_OOM;
         }
@@ -532,6 +540,12 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info) {
             info->ms[i] = ms;
         }
     }
+    return WV_OK;
+}
+
+int wv_batch_set_wait_limit(wv_batch *b, int polls) {
+    if (!b || polls < 0) return WV_ERR_ARG;
+    b->wait_polls = std::min(polls, kBatchWaitPolls);
     return WV_OK;
 }
 

@@ -355,11 +355,14 @@ __device__ __forceinline__ void subband_of(int x, int y, int w, int h, int level
     ysub = y;
 }
 
-// Eq. 3 with the mapping factor H(y) = 1 - sin(pi y / S_y) (Sec. 3.6); the
-// approximation band uses l = l_max (H only).
-__device__ __forceinline__ float paper_threshold(float alpha, int l, int L, int ysub, int sh) {
+// Eq. 3 with the mapping factor H(y) = 1 - sin(pi y / S_y) (Sec. 3.6): the
+// detail bands of level l take alpha ((L - l) / L)^2 + H; the approximation
+// band (l = l_max) takes the level term alone, which is 0 -- H thins the
+// detail the equirectangular mapping oversamples toward the poles, it does
+// not remove the image itself.
+__device__ __forceinline__ float paper_threshold(float alpha, int l, int L, int ysub, int sh, bool approx) {
     const float r = (float)(L - l) / (float)L;
-    return alpha * r * r + 1.0f - sinpif((float)ysub / (float)sh);
+    return alpha * r * r + (approx ? 0.0f : 1.0f - sinpif((float)ysub / (float)sh));
 }
 
 __global__ void k_load_unit(const uint8_t *src, float *dst, size_t n) {
@@ -374,7 +377,7 @@ __global__ void k_threshold(float *c, int w, int h, int levels, float alpha) {
     int lev, ysub, sh;
     subband_of(x, y, w, h, levels, lev, ysub, sh);
     const bool ll = x < (w >> levels) && y < (h >> levels);
-    if (!(fabsf(c[i]) > paper_threshold(alpha, ll ? levels : lev, levels, ysub, sh))) c[i] = 0.f;
+    if (!(fabsf(c[i]) > paper_threshold(alpha, ll ? levels : lev, levels, ysub, sh, ll))) c[i] = 0.f;
 }
 
 // Ordered-integer image of a float (monotonic), for atomic min / max.
@@ -423,7 +426,10 @@ __global__ void k_haar_paper(float *work, size_t plane_elems, int k, int w, int 
         if (valid) {
             c = bands[s];
             const float r = k > 0 ? (float)(k - slot_level[s]) / (float)k : 0.f;
-            const float T = alpha_t * r * r + 1.0f - sinpif((float)ysub / (float)sh);
+            // H on the temporal detail bands' spatial detail only (the low
+            // band and the approximation area keep the level term, 0 / small)
+            const bool approx = ll || s == 0;
+            const float T = alpha_t * r * r + (approx ? 0.0f : 1.0f - sinpif((float)ysub / (float)sh));
             if (!(fabsf(c) > T)) c = 0.f;
             work[(size_t)s * plane_elems + i] = c;
         }

@@ -226,7 +226,7 @@ __device__ __forceinline__ bool fovea_kept(const TileArgs &a, const PlaneGeom &p
 }
 
 // Dequantised, rebuilt coefficient (scalar path for edge chunks).
-template <int WAV, int NB, bool FOV, int QM = 0>
+template <int WAV, int NB, bool FOV, int QM = 0, bool CHK = false>
 __device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, const PlaneGeom &pg, int plane,
                                                          int level, int sub, int kx, int ky) {
     const Geom &g = a.g;
@@ -241,9 +241,11 @@ __device__ __forceinline__ typename Traits<WAV>::T coef1(const TileArgs &a, cons
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-        if (a.n_slots > 0 && slot >= a.n_slots) {   // bad table entry: absent, recorded
-            record_error(a.err, WV_ERR_FORMAT);
-            slot = -1;
+        if constexpr (CHK) {   // entries at or above the payload's block count: absent, recorded
+            if (slot >= a.n_slots) {
+                record_error(a.err, WV_ERR_FORMAT);
+                slot = -1;
+            }
         }
         have[b] = slot >= 0;
         const int v = have[b] ? (int)__ldg(&a.payload[(size_t)slot * bsz + off]) : 0;
@@ -281,7 +283,7 @@ struct Task {
     bool fast;           // chunk entirely inside the subband (no extension)
 };
 
-template <int WAV, int NB, bool FOV>
+template <int WAV, int NB, bool FOV, bool CHK = false>
 __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg, const LevelGeo &G,
                                           const Task &t, Raw<NB> &r) {
     const Geom &g = a.g;
@@ -308,9 +310,11 @@ __device__ __forceinline__ void load_task(const TileArgs &a, const PlaneGeom &pg
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
-            if (a.n_slots > 0 && slot >= a.n_slots) {   // bad table entry: absent, recorded
-                record_error(a.err, WV_ERR_FORMAT);
-                slot = -1;
+            if constexpr (CHK) {   // entries at or above the payload's block count: absent, recorded
+                if (slot >= a.n_slots) {
+                    record_error(a.err, WV_ERR_FORMAT);
+                    slot = -1;
+                }
             }
             if (slot >= 0 && any) {
                 r.have[e][b] = true;
@@ -330,7 +334,7 @@ __device__ __forceinline__ void clear_halves(uint4 (&q)[NB], int keep) {
     }
 }
 
-template <int WAV, int NB, bool FOV, int QM = 0>
+template <int WAV, int NB, bool FOV, int QM = 0, bool CHK = false>
 __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &pg, int plane,
                                             const LevelGeo &G, const Task &t, Raw<NB> &r,
                                             const float *P, int nch, float *A) {
@@ -349,7 +353,7 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
         } else {
 #pragma unroll
             for (int m = 0; m < 8; ++m)
-                od[m] = coef1<WAV, NB, FOV, QM>(a, pg, plane, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
+                od[m] = coef1<WAV, NB, FOV, QM, CHK>(a, pg, plane, G.l, s_odd, refl_sub(kx + m, G.nw, 1), t.ky);
         }
         // even columns: LH (odd row) or LL (even row)
         if (s_even == 2 || G.l == g.levels) {
@@ -359,7 +363,7 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
             } else {
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
-                    ev[m] = coef1<WAV, NB, FOV, QM>(a, pg, plane, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
+                    ev[m] = coef1<WAV, NB, FOV, QM, CHK>(a, pg, plane, G.l, s_even, refl_sub(kx + m, G.nw, 0), t.ky);
             }
         } else if (G.l == a.l_top) {   // LL from a plane written by a coarser pass
             const float *src = a.ll_in[plane] + (size_t)t.ky * a.ll_in_pitch[plane];
@@ -453,7 +457,7 @@ __device__ __forceinline__ void finish_task(const TileArgs &a, const PlaneGeom &
     }
 }
 
-template <int WAV, int NB, bool FOV, int QM = 0>
+template <int WAV, int NB, bool FOV, int QM = 0, bool CHK = false>
 __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &pg, int plane, const LevelGeo &G,
                             const float *P, float *A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -484,8 +488,8 @@ __device__ __forceinline__ void gather_rows(const TileArgs &a, const PlaneGeom &
     for (int base = warp * rpw; base < G.rows; base += stride) {
         const Task t = make(base + r_in);
         Raw<NB> r;
-        load_task<WAV, NB, FOV>(a, pg, G, t, r);
-        finish_task<WAV, NB, FOV, QM>(a, pg, plane, G, t, r, P, nch, A);
+        load_task<WAV, NB, FOV, CHK>(a, pg, G, t, r);
+        finish_task<WAV, NB, FOV, QM, CHK>(a, pg, plane, G, t, r, P, nch, A);
     }
 }
 
@@ -643,7 +647,7 @@ __device__ __forceinline__ void column_pair(const float *A, int sa, int col, int
 
 // Decode one tile (entry: plane << 28 | ty << 14 | tx) of a pass: levels
 // l_top down to l_bot; A and P are the CTA's shared arrays.
-template <int WAV, int NB, bool FOV, int QM = 0>
+template <int WAV, int NB, bool FOV, int QM = 0, bool CHK = false>
 __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float *A, float *P) {
     constexpr int H = Traits<WAV>::H;
     const Geom &g = a.g;
@@ -669,7 +673,7 @@ __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float 
             return;
         }
         // 1. gather + horizontal synthesis into A
-        gather_rows<WAV, NB, FOV, QM>(a, pg, plane, G, P, A);
+        gather_rows<WAV, NB, FOV, QM, CHK>(a, pg, plane, G, P, A);
         __syncthreads();
         // 2. vertical synthesis of the columns the outputs need
         const int nv = G.ox.hi - G.ox.lo + 1;
@@ -764,13 +768,13 @@ __device__ __forceinline__ void decode_one(const TileArgs &a, uint32_t e, float 
     }
 }
 
-template <int WAV, int NB, int QM>
+template <int WAV, int NB, int QM, bool CHK = false>
 __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
     extern __shared__ __align__(16) float smem[];
     float *A = smem;
     float *P = smem + a.a_floats;
     const int count = *(volatile const int *)a.count;
-    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) decode_one<WAV, NB, false, QM>(a, a.tiles[ti], A, P);
+    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) decode_one<WAV, NB, false, QM, CHK>(a, a.tiles[ti], A, P);
 }
 
 // ---- batched decode: one persistent launch over all surfaces ---------------
@@ -780,10 +784,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tiles(TileArgs a) {
 // bounded) until all coarse tiles of its surface are finished.  No wait can
 // block forever: when a fine item is dispensed, every coarse item has already
 // been dispensed to a running CTA, and coarse items never wait.  After
-// kMaxSpins polls the wait gives up, records WV_ERR_TIMEOUT and decodes
-// anyway (all reads stay in bounds).
-
-constexpr int kMaxSpins = 1 << 21;
+// a number of polls (the batch's wait limit, at most kBatchWaitPolls) the
+// wait gives up, records WV_ERR_TIMEOUT and decodes anyway (all reads stay
+// in bounds).
 
 __device__ __forceinline__ int load_acquire(const int *p) {
     int v;
@@ -791,8 +794,8 @@ __device__ __forceinline__ int load_acquire(const int *p) {
     return v;
 }
 
-__device__ __forceinline__ bool wait_at_least(const int *flag, int target) {
-    for (int it = 0; it < kMaxSpins; ++it) {
+__device__ __forceinline__ bool wait_at_least(const int *flag, int target, int polls) {
+    for (int it = 0; it < polls; ++it) {
         if (load_acquire(flag) >= target) return true;
         __nanosleep(256);
     }
@@ -802,7 +805,7 @@ __device__ __forceinline__ bool wait_at_least(const int *flag, int target) {
 template <int WAV, int NB, bool FOV, int QM>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tiles_batch(const SurfaceJob *__restrict__ surfs, const uint2 *__restrict__ coarse,
-                  const uint2 *__restrict__ fine, int *cls, int *surf, int *err) {
+                  const uint2 *__restrict__ fine, int *cls, int *surf, int *err, const int *wait_polls) {
     extern __shared__ __align__(16) float smem[];
     __shared__ TileArgs sa;
     __shared__ uint2 s_item;
@@ -820,7 +823,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 s_item = w;
                 s_kind = 1;
                 const int *c = surf + 2 * (int)w.x;
-                if (!wait_at_least(c + 1, c[0])) record_error(err, WV_ERR_TIMEOUT);
+                const int polls = min(max(__ldg(wait_polls), 0), kBatchWaitPolls);
+                if (!wait_at_least(c + 1, c[0], polls)) record_error(err, WV_ERR_TIMEOUT);
             } else {
                 s_kind = 2;
             }
@@ -921,7 +925,7 @@ void fill_tile_scales(TileArgs &a) {
 
 namespace {
 
-template <int WAV, int NB, int QM = 0>
+template <int WAV, int NB, int QM = 0, bool CHK = false>
 cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
     // largest dynamic shared memory opted in so far, per device
     static int opted[64] = {};
@@ -929,17 +933,17 @@ cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) 
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || smem > opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB, QM, CHK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) opted[dev] = smem;
     }
-    k_tiles<WAV, NB, QM><<<grid, threads, smem, cs>>>(a);
+    k_tiles<WAV, NB, QM, CHK><<<grid, threads, smem, cs>>>(a);
     return cudaGetLastError();
 }
 
 template <int WAV, int NB, bool FOV, int QM>
 cudaError_t launch_batch_t(const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
-                           int *cls, int *surf, int *err, int smem_bytes, cudaStream_t cs) {
+                           int *cls, int *surf, int *err, const int *wait_polls, int smem_bytes, cudaStream_t cs) {
     static int opted[64] = {};
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
@@ -954,7 +958,7 @@ cudaError_t launch_batch_t(const SurfaceJob *surfs, const uint2 *coarse, const u
                                                                   smem_bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    k_tiles_batch<WAV, NB, FOV, QM><<<sms * per_sm, kThreads, smem_bytes, cs>>>(surfs, coarse, fine, cls, surf, err);
+    k_tiles_batch<WAV, NB, FOV, QM><<<sms * per_sm, kThreads, smem_bytes, cs>>>(surfs, coarse, fine, cls, surf, err, wait_polls);
     return cudaGetLastError();
 }
 
@@ -966,6 +970,23 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
     const int threads = coarse ? kThreads / 2 : kThreads;
     const int grid = decode_tiles_grid(a.g) * (coarse ? 2 : 1);
     const int nb = a.bands.n;
+    if (a.n_slots > 0) {   // table entries checked against the payload's block count (q codes only)
+        if (a.g.quant != 0 || a.g.dz_t) return cudaErrorInvalidValue;
+        if (a.g.wavelet == WV_WAVELET_97) {
+            switch (nb) {
+            case 1: return launch_t<1, 1, 0, true>(a, grid, threads, cs);
+            case 2: return launch_t<1, 2, 0, true>(a, grid, threads, cs);
+            case 3: return launch_t<1, 3, 0, true>(a, grid, threads, cs);
+            default: return launch_t<1, 4, 0, true>(a, grid, threads, cs);
+            }
+        }
+        switch (nb) {
+        case 1: return launch_t<0, 1, 0, true>(a, grid, threads, cs);
+        case 2: return launch_t<0, 2, 0, true>(a, grid, threads, cs);
+        case 3: return launch_t<0, 3, 0, true>(a, grid, threads, cs);
+        default: return launch_t<0, 4, 0, true>(a, grid, threads, cs);
+        }
+    }
     if (a.g.quant == 1) {   // paper-faithful byte quantiser (9/7 only)
         switch (nb) {
         case 1: return launch_t<1, 1, 1>(a, grid, threads, cs);
@@ -1091,26 +1112,26 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
 // (surfaces whose coefficient frames number nb).
 template <int WAV, bool FOV, int QM>
 cudaError_t launch_batch_nb(int nb, const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
-                            int *cls_ctr, int *surf_ctr, int *err, int smem_bytes, cudaStream_t cs) {
+                            int *cls_ctr, int *surf_ctr, int *err, const int *wait_polls, int smem_bytes, cudaStream_t cs) {
     switch (nb) {
-    case 1: return launch_batch_t<WAV, 1, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    case 2: return launch_batch_t<WAV, 2, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    case 3: return launch_batch_t<WAV, 3, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    default: return launch_batch_t<WAV, 4, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+    case 1: return launch_batch_t<WAV, 1, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
+    case 2: return launch_batch_t<WAV, 2, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
+    case 3: return launch_batch_t<WAV, 3, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
+    default: return launch_batch_t<WAV, 4, FOV, QM>(surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
     }
 }
 
 cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
                                 const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
-                                int *err, int smem_bytes, cudaStream_t cs) {
+                                int *err, const int *wait_polls, int smem_bytes, cudaStream_t cs) {
     if (wavelet == WV_WAVELET_97 && dz_t)
-        return fovea ? launch_batch_nb<1, true, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
-                     : launch_batch_nb<1, false, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+        return fovea ? launch_batch_nb<1, true, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs)
+                     : launch_batch_nb<1, false, 2>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
     if (wavelet == WV_WAVELET_97)
-        return fovea ? launch_batch_nb<1, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
-                     : launch_batch_nb<1, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
-    return fovea ? launch_batch_nb<0, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs)
-                 : launch_batch_nb<0, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, smem_bytes, cs);
+        return fovea ? launch_batch_nb<1, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs)
+                     : launch_batch_nb<1, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
+    return fovea ? launch_batch_nb<0, true, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs)
+                 : launch_batch_nb<0, false, 0>(nb, surfs, coarse, fine, cls_ctr, surf_ctr, err, wait_polls, smem_bytes, cs);
 }
 
 // ---- dead-zone codes as 2q + sign(q) -----------------------------------------

@@ -836,6 +836,25 @@ int wv_cnn_set_params(wv_cnn *c, const float *host) {
                                                                                                        : WV_ERR_CUDA;
 }
 
+int wv_cnn_get_state(wv_cnn *c, float *m_host, float *v_host, int *steps) {
+    if (!c || !m_host || !v_host || !steps) return WV_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(m_host, c->m, sizeof(float) * kParams, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(v_host, c->v, sizeof(float) * kParams, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return WV_ERR_CUDA;
+    *steps = c->step;
+    return WV_OK;
+}
+
+int wv_cnn_set_state(wv_cnn *c, const float *m_host, const float *v_host, int steps) {
+    if (!c || !m_host || !v_host || steps < 0) return WV_ERR_ARG;
+    if (cudaMemcpy(c->m, m_host, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->v, v_host, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess)
+        return WV_ERR_CUDA;
+    c->step = steps;
+    return WV_OK;
+}
+
 int wv_cnn_forward(wv_cnn *c, const float *x_dev, float *y_dev, int n, int h, int w, void *cuda_stream) {
     if (!c || !x_dev || !y_dev || check_dims(n, h, w) != WV_OK) return WV_ERR_ARG;
     if (ensure_workspace(c, (size_t)n * h * w) != WV_OK) return WV_ERR_OOM;

@@ -282,7 +282,13 @@ cudaError_t payload_max_abs(const int16_t *payload, size_t count, int *dev_word,
 cudaError_t payload_to_deadzone_t(int16_t *payload, size_t count, cudaStream_t cs);
 cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
                                 const uint2 *coarse, const uint2 *fine, int *cls_ctr, int *surf_ctr,
-                                int *err, int smem_bytes, cudaStream_t cs);
+                                int *err, const int *wait_polls, int smem_bytes, cudaStream_t cs);
+// Polls of a batch's bounded device wait before it gives up (the default and
+// the largest a batch accepts; wv_batch_set_wait_limit lowers it)
+constexpr int kBatchWaitPolls = 1 << 21;
+// Device allocations of the library (stream stores, batch arenas): cudaMalloc,
+// unless a failure was injected with wv_debug_fail_device_allocs.
+cudaError_t dev_alloc(void **p, size_t bytes);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);

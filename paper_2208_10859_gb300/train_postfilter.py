@@ -69,6 +69,61 @@ def psnr(a, b) -> float:
     return 10 * math.log10(1.0 / mse)
 
 
+def save_checkpoint(path: str, net, it: int, gen, log, torch) -> None:
+    """Everything an interrupted run needs to continue exactly: parameters,
+    Adam moments and step count, the iteration, the sampling generator's
+    state and the loss log (a torch.save dict)."""
+    m, v, k = net.state()
+    torch.save({"params": net.params(), "adam_m": m, "adam_v": v, "adam_steps": k, "iteration": it,
+                "rng": gen.get_state(), "log": list(log)}, path + ".tmp")
+    os.replace(path + ".tmp", path)
+
+
+def load_checkpoint(path: str, net, gen, torch):
+    """Restore a checkpoint into net and gen; returns (iteration, log)."""
+    ck = torch.load(path, weights_only=False)
+    net.set_params(ck["params"])
+    net.set_state(ck["adam_m"], ck["adam_v"], ck["adam_steps"])
+    gen.set_state(ck["rng"])
+    return int(ck["iteration"]), list(ck["log"])
+
+
+def patch_pool(dec, n: int, patch: int, seed: int, torch):
+    """The training set: n crops (frame, row, column) of patch x patch pairs,
+    drawn once from the seed."""
+    g = torch.Generator(device="cpu").manual_seed(seed + 7919)
+    nfr, hh, ww = dec.shape
+    return (torch.randint(0, nfr, (n,), generator=g), torch.randint(0, hh - patch + 1, (n,), generator=g),
+            torch.randint(0, ww - patch + 1, (n,), generator=g))
+
+
+def train(net, dec, org, pool, gen, steps: int, batch: int, patch: int, lr0: float, torch, start: int = 0,
+          stop: int | None = None, log=None, checkpoint: str | None = None, every: int = 0,
+          log_every: int = 200):
+    """Adam on batches of the pool's patch pairs for iterations start .. stop - 1
+    of a run of `steps` (cosine decay of the learning rate over the run);
+    batches are drawn from gen.  Writes a checkpoint every `every` iterations
+    and at the end when a path is given.  Returns the loss log [(iteration,
+    loss)]."""
+    log = [] if log is None else log
+    stop = steps if stop is None else min(stop, steps)
+    idx, ys, xs = pool
+    for it in range(start, stop):
+        sel = torch.randint(0, idx.shape[0], (batch,), generator=gen).tolist()
+        xb = torch.stack([dec[idx[k], ys[k]:ys[k] + patch, xs[k]:xs[k] + patch] for k in sel])
+        tb = torch.stack([org[idx[k], ys[k]:ys[k] + patch, xs[k]:xs[k] + patch] for k in sel])
+        lr = lr0 * (0.5 * (1 + math.cos(math.pi * it / steps)) * 0.9 + 0.1)
+        loss = net.train_step(xb.contiguous(), tb.contiguous(), lr, want_loss=(it % log_every == 0))
+        if loss is not None:
+            log.append((it, loss))
+            print(f"step {it}/{steps} loss {loss:.3e}", flush=True)
+        if checkpoint and every and (it + 1) % every == 0:
+            save_checkpoint(checkpoint, net, it + 1, gen, log, torch)
+    if checkpoint:
+        save_checkpoint(checkpoint, net, stop, gen, log, torch)
+    return log
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--step", type=float, required=True, choices=STEPS)
@@ -78,6 +133,9 @@ def main():
     ap.add_argument("--epochs", type=float, default=2.0)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--checkpoint", default=None, help="checkpoint file (written every --every iterations)")
+    ap.add_argument("--every", type=int, default=500)
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     args = ap.parse_args()
     import torch
     sys.path.insert(0, ROOT)
@@ -89,23 +147,15 @@ def main():
     dec, org = coded_pairs(wv, torch, (101, 102, 103, 104, 105, 106), (args.step,))
     tdec, torg = coded_pairs(wv, torch, (201,), (args.step,), frames_per_seed=4)
     g = torch.Generator(device="cpu").manual_seed(args.seed)
-    nfr = dec.shape[0]
-    idx = torch.randint(0, nfr, (args.patches,), generator=g)
-    ys = torch.randint(0, SIZE - PATCH + 1, (args.patches,), generator=g)
-    xs = torch.randint(0, SIZE - PATCH + 1, (args.patches,), generator=g)
     net = wv.CNN(seed=args.seed)
     steps = int(args.epochs * args.patches / args.batch)
-    log = []
+    pool = patch_pool(dec, args.patches, PATCH, args.seed, torch)
+    start, log = 0, []
+    if args.resume:
+        start, log = load_checkpoint(args.checkpoint, net, g, torch)
     t1 = time.time()
-    for it in range(steps):
-        sel = torch.randint(0, args.patches, (args.batch,), generator=g)
-        xb = torch.stack([dec[idx[k], ys[k]:ys[k] + PATCH, xs[k]:xs[k] + PATCH] for k in sel.tolist()])
-        tb = torch.stack([org[idx[k], ys[k]:ys[k] + PATCH, xs[k]:xs[k] + PATCH] for k in sel.tolist()])
-        lr = args.lr * (0.5 * (1 + math.cos(math.pi * it / steps)) * 0.9 + 0.1)
-        loss = net.train_step(xb.contiguous(), tb.contiguous(), lr, want_loss=(it % 200 == 0))
-        if loss is not None:
-            log.append((it, loss))
-            print(f"step {it}/{steps} loss {loss:.3e}", flush=True)
+    log = train(net, dec, org, pool, g, steps, args.batch, PATCH, args.lr, torch, start=start, log=log,
+                checkpoint=args.checkpoint, every=args.every)
     torch.cuda.synchronize()
     train_s = time.time() - t1
     if net.sync_status() != 0:

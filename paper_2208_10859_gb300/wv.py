@@ -129,6 +129,8 @@ def _lib():
             "wv_cnn_close": (None, [vp]),
             "wv_cnn_get_params": (c_int, [vp, vp]),
             "wv_cnn_set_params": (c_int, [vp, vp]),
+            "wv_cnn_get_state": (c_int, [vp, vp, vp, ctypes.POINTER(c_int)]),
+            "wv_cnn_set_state": (c_int, [vp, vp, vp, c_int]),
             "wv_cnn_forward": (c_int, [vp, vp, vp, c_int, c_int, c_int, vp]),
             "wv_cnn_gradients": (c_int, [vp, vp, vp, c_int, c_int, c_int, vp, ctypes.POINTER(fl), vp]),
             "wv_cnn_train_step": (c_int, [vp, vp, vp, c_int, c_int, c_int, fl, ctypes.POINTER(fl), vp]),
@@ -158,6 +160,8 @@ def _lib():
             "wv_batch_stats": (c_int, [vp, ctypes.POINTER(BatchInfo)]),
             "wv_batch_set_timing": (c_int, [vp, c_int]),
             "wv_batch_set_sharing": (c_int, [vp, c_int]),
+            "wv_batch_set_wait_limit": (c_int, [vp, c_int]),
+            "wv_debug_fail_device_allocs": (None, [c_int]),
             "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int]),
             "wv_batch_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
                                             ctypes.POINTER(c_int)]),
@@ -184,6 +188,7 @@ def exported_symbols() -> list[str]:
             "wv_encode_sizes", "wv_encode", "wv_decode_plane_static", "wv_release_default_batch",
             "wv_cone_bytes_fovea", "wv_cone_bytes_split", "wv_request_bytes", "wv_encode_paper",
             "wv_cnn_param_count", "wv_cnn_create", "wv_cnn_close", "wv_cnn_get_params", "wv_cnn_set_params",
+            "wv_cnn_get_state", "wv_cnn_set_state",
             "wv_cnn_forward", "wv_cnn_gradients", "wv_cnn_train_step", "wv_cnn_sync_status",
             "wv_decode_viewport_filtered",
             "wv_server_create", "wv_server_add_stream", "wv_server_submit", "wv_server_poll",
@@ -191,7 +196,7 @@ def exported_symbols() -> list[str]:
             "wv_server_reset_stats", "wv_server_close",
             "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
-            "wv_batch_set_sharing",
+            "wv_batch_set_sharing", "wv_batch_set_wait_limit", "wv_debug_fail_device_allocs",
             "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
 
 
@@ -427,6 +432,10 @@ class Batch:
     def set_sharing(self, on: bool) -> None:
         _check(_lib().wv_batch_set_sharing(self._h, 1 if on else 0), "wv_batch_set_sharing")
 
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of the tile decode's bounded wait before it gives up."""
+        _check(_lib().wv_batch_set_wait_limit(self._h, int(polls)), "wv_batch_set_wait_limit")
+
     def set_tile_shape(self, wavelet, levels, width, height, tile, ctile) -> None:
         _check(_lib().wv_batch_set_tile_shape(self._h, wavelet, levels, width, height, tile, ctile),
                "wv_batch_set_tile_shape")
@@ -613,6 +622,21 @@ class CNN:
     def set_params(self, p) -> None:
         p = np.ascontiguousarray(p, np.float32)
         _check(_lib().wv_cnn_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)), "wv_cnn_set_params")
+
+    def state(self) -> tuple[np.ndarray, np.ndarray, int]:
+        """Adam moments (m, v) and the number of steps taken."""
+        m = np.empty(self.param_count(), np.float32)
+        v = np.empty(self.param_count(), np.float32)
+        k = ctypes.c_int()
+        _check(_lib().wv_cnn_get_state(self.handle, m.ctypes.data_as(ctypes.c_void_p),
+                                       v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)), "wv_cnn_get_state")
+        return m, v, int(k.value)
+
+    def set_state(self, m, v, steps: int) -> None:
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        _check(_lib().wv_cnn_set_state(self.handle, m.ctypes.data_as(ctypes.c_void_p),
+                                       v.ctypes.data_as(ctypes.c_void_p), int(steps)), "wv_cnn_set_state")
 
     def forward(self, x, stream=None):
         import torch

@@ -154,3 +154,44 @@ def test_filtered_viewport_with_zero_residual_is_the_plain_viewport():
     d = np.abs(c.cpu().numpy().astype(int) - a.cpu().numpy().astype(int))
     assert d.max() > 0 and np.all(c.cpu().numpy()[..., 3] == 255)
     assert s.sync_status() == 0 and net.sync_status() == 0
+
+
+def test_checkpoint_resume_equals_unbroken_run(tmp_path):
+    """Training checkpointed half-way and resumed in a new network object
+    (parameters, Adam moments and step count, sampling generator, loss log)
+    follows the unbroken run: the same losses at every logged step and the
+    same final parameters."""
+    from paper_2208_10859_gb300 import wv
+    from paper_2208_10859_gb300 import train_postfilter as TP
+    rng = np.random.default_rng(12)
+    org = torch.tensor(rng.uniform(0.2, 0.8, (3, 96, 96)), dtype=torch.float32, device="cuda")
+    dec = (org + torch.tensor(rng.normal(0, 0.02, (3, 96, 96)), dtype=torch.float32, device="cuda")).contiguous()
+    pool = TP.patch_pool(dec, 40, 48, 3, torch)
+    steps, batch = 12, 4
+
+    def run(split):
+        net = wv.CNN(seed=5)
+        gen = torch.Generator(device="cpu").manual_seed(9)
+        ck = str(tmp_path / f"ck{int(split)}.pt")
+        if not split:
+            log = TP.train(net, dec, org, pool, gen, steps, batch, 48, 1e-3, torch, log_every=1)
+            return log, net
+        log = TP.train(net, dec, org, pool, gen, steps, batch, 48, 1e-3, torch, stop=5, checkpoint=ck, log_every=1)
+        net.close()
+        net2 = wv.CNN(seed=77)                        # other initial parameters, no state
+        gen2 = torch.Generator(device="cpu").manual_seed(1234)
+        start, log2 = TP.load_checkpoint(ck, net2, gen2, torch)
+        assert start == 5 and log2 == log
+        log2 = TP.train(net2, dec, org, pool, gen2, steps, batch, 48, 1e-3, torch, start=start, log=log2,
+                        log_every=1)
+        return log2, net2
+
+    log_a, net_a = run(False)
+    log_b, net_b = run(True)
+    assert [i for i, _ in log_a] == [i for i, _ in log_b] == list(range(steps))
+    np.testing.assert_allclose([l for _, l in log_b], [l for _, l in log_a], rtol=1e-5, atol=0)
+    np.testing.assert_allclose(net_b.params(), net_a.params(), rtol=1e-5, atol=1e-7)
+    assert net_a.state()[2] == net_b.state()[2] == steps
+    assert net_a.sync_status() == 0 and net_b.sync_status() == 0
+    net_a.close()
+    net_b.close()

@@ -22,12 +22,40 @@ def test_mapping_factor_closed_form():
 
 def test_threshold_map_follows_eq3():
     T = PF.threshold_map(64, 32, 3, 0.4)
-    # LL_3 (8 x 4): H only
-    np.testing.assert_allclose(T[:4, :8], np.repeat(PF.mapping_factor(4)[:, None], 8, 1))
+    # LL_3 (8 x 4): l = l_max, the level term is 0 and H applies to details only
+    np.testing.assert_array_equal(T[:4, :8], 0.0)
+    # HL_3 (8 x 4): alpha ((3 - 3) / 3)^2 + H = H
+    np.testing.assert_allclose(T[:4, 8:16], np.repeat(PF.mapping_factor(4)[:, None], 8, 1))
     # HH_1 (32 x 16): alpha ((3 - 1) / 3)^2 + H
     np.testing.assert_allclose(T[16:, 32:], 0.4 * (2 / 3) ** 2 + np.repeat(PF.mapping_factor(16)[:, None], 32, 1))
     # HL_2: alpha (1/3)^2 + H
     np.testing.assert_allclose(T[:8, 16:32], 0.4 / 9 + np.repeat(PF.mapping_factor(8)[:, None], 16, 1))
+
+
+def test_temporal_threshold_map_closed_form():
+    k = 2
+    # the low band (j = 0): level term alpha_t ((k - k) / k)^2 = 0 everywhere
+    np.testing.assert_array_equal(PF.temporal_threshold_map(64, 32, 3, 0.3, 0, k), 0.0)
+    # a detail frame of temporal level j = 1: alpha_t ((2 - 1) / 2)^2, plus H on
+    # the spatial detail bands, none on the approximation area
+    T = PF.temporal_threshold_map(64, 32, 3, 0.3, 1, k)
+    np.testing.assert_allclose(T[:4, :8], 0.3 / 4)
+    np.testing.assert_allclose(T[16:, 32:], 0.3 / 4 + np.repeat(PF.mapping_factor(16)[:, None], 32, 1))
+
+
+def test_constant_frames_survive_at_every_row():
+    """A constant frame has energy in the approximation band only; with H on
+    the detail bands only, it decodes to itself at every row, the poles
+    included (H = 1 there would otherwise zero it)."""
+    frames = [(np.full((64, 64), 200, np.uint8), np.full((32, 32), 90, np.uint8),
+               np.full((32, 32), 160, np.uint8))] * 4
+    pp = PF.PaperParams(64, 64, 3, 1, 3, 4, 2, alpha=0.25, alpha_t=0.005)
+    st = PF.PaperStream(PF.encode(frames, pp))
+    for f in range(4):
+        for pl, v in enumerate((200, 90, 160)):
+            x, u8 = st.decode_plane(f, pl)
+            # the extremes are stored as float32: a rounding of ~1e-7 relative remains
+            assert np.abs(x - v).max() < 1e-3, (f, pl, np.abs(x - v).max())
 
 
 def test_byte_quantiser_extremes_and_error():
@@ -58,7 +86,9 @@ def _loop_reference(frame, pp):
     for (name, lev, x0, y0, sw, sh) in O.subbands(w, h, pp.levels):
         l = pp.levels if name == "LL" else lev
         for yy in range(sh):
-            T = pp.alpha * ((pp.levels - l) / pp.levels) ** 2 + 1 - math.sin(math.pi * yy / sh)
+            # H(y) on the detail bands; the approximation band keeps the level term
+            H = 0.0 if name == "LL" else 1 - math.sin(math.pi * yy / sh)
+            T = pp.alpha * ((pp.levels - l) / pp.levels) ** 2 + H
             for xx in range(sw):
                 keep[y0 + yy, x0 + xx] = abs(c[y0 + yy, x0 + xx]) > T
     approx = np.zeros_like(keep)
