@@ -32,6 +32,16 @@ __device__ __forceinline__ Taps bilinear_taps(int w, int r_lo, int r_n, float u,
     int x0, fx, y0, fy;
     fixed_split(u, x0, fx);
     fixed_split(v, y0, fy);
+    Taps t;
+    t.fx = fx;
+    t.fy = fy;
+    if ((unsigned)x0 < (unsigned)(w - 1) && y0 >= r_lo && y0 < r_lo + r_n - 1) {   // no wrap, no clamp
+        t.a0 = y0 * w + x0;
+        t.a1 = t.a0 + 1;
+        t.b0 = t.a0 + w;
+        t.b1 = t.b0 + 1;
+        return t;
+    }
     int xa = x0;
     if (xa < 0) xa += w;
     else if (xa >= w) xa -= w;
@@ -42,13 +52,10 @@ __device__ __forceinline__ Taps bilinear_taps(int w, int r_lo, int r_n, float u,
     const int xb = (xa + 1 == w) ? 0 : xa + 1;
     const int ya = min(max(y0, r_lo), r_lo + r_n - 1) * w;
     const int yb = min(max(y0 + 1, r_lo), r_lo + r_n - 1) * w;
-    Taps t;
     t.a0 = ya + xa;
     t.a1 = ya + xb;
     t.b0 = yb + xa;
     t.b1 = yb + xb;
-    t.fx = fx;
-    t.fy = fy;
     return t;
 }
 

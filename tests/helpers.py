@@ -136,9 +136,11 @@ def other_rounding(x: np.ndarray, eps: float = 2e-3) -> np.ndarray:
 def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov, eye: int = 0):
     """Per-pixel bound (eps_u, eps_v) in pixels on the float32 position error
     of the device projection: direction components carry a few float32
-    rounding errors (~4e-7 relative), atan2f adds at most 2 ulp, and the
-    longitude error is amplified by 1/cos(latitude) near the poles; a final
-    rounding of u (v) adds half an ulp of the frame width (height)."""
+    rounding errors (~4e-7 relative), the device atan2 (a degree-9
+    polynomial in t^2 after a hardware reciprocal) adds at most 4 ulp of an
+    angle up to pi (1e-6 rad), and the longitude error is amplified by
+    1/cos(latitude) near the poles; a final rounding of u (v) adds half an
+    ulp of the frame width (height)."""
     t = math.tan(fov / 2)
     xn = (2 * (np.arange(out_w) + 0.5) / out_w - 1) * t
     yn = (1 - 2 * (np.arange(out_h) + 0.5) / out_h) * t
@@ -149,8 +151,8 @@ def position_error_bound(p: O.Params, out_w, out_h, yaw, pitch, fov, eye: int = 
     coslat = np.hypot(d[..., 0], d[..., 2]) / norm
     ku = p.width / (2 * math.pi)
     kv = O.eye_rows(p, eye)[1] / math.pi
-    eps_u = ku * (1.5e-6 / np.maximum(coslat, 1e-9) + 5e-7) + p.width * 2.0 ** -23
-    eps_v = np.full_like(eps_u, kv * 1.5e-6 + p.height * 2.0 ** -23)
+    eps_u = ku * (1.5e-6 / np.maximum(coslat, 1e-9) + 1e-6) + p.width * 2.0 ** -23
+    eps_v = np.full_like(eps_u, kv * (1.5e-6 + 1e-6) + p.height * 2.0 ** -23)
     return eps_u, eps_v
 
 
