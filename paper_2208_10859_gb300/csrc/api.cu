@@ -21,7 +21,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "wv_impl.h"
@@ -464,6 +467,20 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
         if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
     }
     return cudaMalloc(p, bytes);
+}
+
+cudaError_t opt_in_smem(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> opted;   // (kernel, device) -> bytes set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &have = opted[std::make_pair(fn, dev)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 namespace {

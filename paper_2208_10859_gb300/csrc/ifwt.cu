@@ -927,16 +927,9 @@ namespace {
 
 template <int WAV, int NB, int QM = 0, bool CHK = false>
 cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
-    // largest dynamic shared memory opted in so far, per device
-    static int opted[64] = {};
     const int smem = (a.a_floats + a.p_floats) * 4;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || smem > opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles<WAV, NB, QM, CHK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) opted[dev] = smem;
-    }
+    cudaError_t e = opt_in_smem(reinterpret_cast<const void *>(k_tiles<WAV, NB, QM, CHK>), smem);
+    if (e != cudaSuccess) return e;
     k_tiles<WAV, NB, QM, CHK><<<grid, threads, smem, cs>>>(a);
     return cudaGetLastError();
 }
@@ -944,17 +937,12 @@ cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) 
 template <int WAV, int NB, bool FOV, int QM>
 cudaError_t launch_batch_t(const SurfaceJob *surfs, const uint2 *coarse, const uint2 *fine,
                            int *cls, int *surf, int *err, const int *wait_polls, int smem_bytes, cudaStream_t cs) {
-    static int opted[64] = {};
     int dev = 0, sms = 148, per_sm = 0;
+    cudaError_t e = opt_in_smem(reinterpret_cast<const void *>(k_tiles_batch<WAV, NB, FOV, QM>), smem_bytes);
+    if (e != cudaSuccess) return e;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || smem_bytes > opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles_batch<WAV, NB, FOV, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_bytes);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) opted[dev] = smem_bytes;
-    }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_batch<WAV, NB, FOV, QM>, kThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_batch<WAV, NB, FOV, QM>, kThreads,
                                                                   smem_bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;

@@ -640,15 +640,9 @@ ConvArgs conv_args(wv_cnn *c, int n, int h, int w) {
 }
 
 cudaError_t launch_mid(const ConvArgs &a, int nb, cudaStream_t cs) {
-    static int opted[64] = {};
     const int smem = 3 * kSlot + kBMid;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        opted[dev] = 1;
-    }
+    cudaError_t e = opt_in_smem(reinterpret_cast<const void *>(k_conv_mid), smem);
+    if (e != cudaSuccess) return e;
     // one work item (strip) per CTA: measured faster than persistent CTAs
     const int items = ((a.w + kTilePx - 1) / kTilePx) * ((a.h + kStrip - 1) / kStrip) * a.n;
     k_conv_mid<<<items, 128, smem, cs>>>(a, nb);
@@ -663,14 +657,8 @@ cudaError_t launch_in1(const ConvArgs &a, cudaStream_t cs) {
 
 cudaError_t launch_wgrad_mid(const bf16 *act, const bf16 *dz, int n, int h, int w, float *dW, float *db, int *err,
                              cudaStream_t cs) {
-    static int opted[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !opted[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_wgrad_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem);
-        if (e != cudaSuccess) return e;
-        opted[dev] = 1;
-    }
+    cudaError_t e = opt_in_smem(reinterpret_cast<const void *>(k_wgrad_mid), kWSmem);
+    if (e != cudaSuccess) return e;
     const int total = n * h * ((w + kWChunk - 1) / kWChunk);
     const int grid = std::max(1, std::min(total, 3 * sm_count()));
     k_wgrad_mid<<<grid, 128, kWSmem, cs>>>(act, dz, n, h, w, dW, db, err);

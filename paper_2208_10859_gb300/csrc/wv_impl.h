@@ -289,6 +289,10 @@ constexpr int kBatchWaitPolls = 1 << 21;
 // Device allocations of the library (stream stores, batch arenas): cudaMalloc,
 // unless a failure was injected with wv_debug_fail_device_allocs.
 cudaError_t dev_alloc(void **p, size_t bytes);
+// Raises kernel fn's dynamic shared memory limit on the current device to at
+// least `bytes` (never lowers it); one lock covers the check and the set, so
+// concurrent launches from several host threads cannot undo each other.
+cudaError_t opt_in_smem(const void *fn, int bytes);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);
