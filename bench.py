@@ -277,6 +277,7 @@ def batched_leg(args, dev, frames8k, stream):
     b.set_timing(True)
     b.decode(reqs)
     stage_ms = b.stats()["ms"]
+    done_b = b.completion_ms(len(reqs))
     b.set_timing(False)
     # plain: the same requests one after the other, one request per launch
     # sequence; completion time of each request within the burst
@@ -320,10 +321,13 @@ def batched_leg(args, dev, frames8k, stream):
         "viewports_per_s": {"batched": BATCH_REQUESTS / (batch_ms / 1e3),
                             "plain_per_viewport": BATCH_REQUESTS / (plain_ms / 1e3),
                             "plain_unfoveated": BATCH_REQUESTS / (unfov_ms / 1e3)},
-        "burst_latency_ms": {"note": "all 256 requests arrive at t=0; a request's latency is its completion time",
-                             "batched_p50": batch_ms, "batched_p99": batch_ms,
+        "burst_latency_ms": {"note": "all 256 requests arrive at t=0; a request's latency is its completion time "
+                                     "(batched: the end of its wave, timed with events between the waves)",
+                             "batched_p50": float(np.percentile(done_b, 50)),
+                             "batched_p99": float(np.percentile(done_b, 99)),
                              "plain_p50": pct(50), "plain_p99": pct(99)},
         "batch_ms": batch_ms, "steps": steps, "stage_ms": stage_ms,
+        "waves": info["waves"],
         "surfaces": info["surfaces"], "coarse_tiles": info["coarse_tiles"], "fine_tiles": info["fine_tiles"],
         "arena_bytes": info["bytes"], "tile_shapes": shapes,
         "outputs_identical_batched_vs_plain": bool(same),

@@ -239,28 +239,35 @@ typedef struct {
     int fine_tiles;      /* output tiles decoded (levels 2..1) */
     size_t bytes;        /* device memory held by the context */
     double ms[4];        /* with wv_batch_set_timing(b, 1): footprint, tile
-                            lists, tile decode, reprojection (milliseconds) */
+                            lists, tile decode, reprojection (milliseconds,
+                            summed over the waves) */
+    int waves;           /* waves of decode targets the batch ran in */
 } wv_batch_info;
 
 /* Create a batch context on the current device whose launches go to
  * cuda_stream (NULL = legacy default stream).  The context allocates its
  * device memory (per decode target: reconstruction and LL_2 planes, tile
  * stamps and lists) and a pinned host staging buffer on demand, growing them
- * when a batch needs more; it never shrinks them before wv_batch_close. */
+ * when a batch needs more; it never shrinks them before wv_batch_close.
+ * Decode targets run in waves that share one device region (see
+ * wv_batch_set_memory_limit), so the device memory stays bounded by the
+ * limit plus the job tables whatever the number of requests. */
 int wv_batch_create(void *cuda_stream, wv_batch **out);
 
 /* Wait for the context's work and free it. */
 void wv_batch_close(wv_batch *b);
 
-/* Decode n requests as one batch: one CUDA graph of (1) the upload of the
- * job tables from pinned host memory, (2) clearing of stamps and counters,
- * (3) the footprint of every request, (4) the tile lists of every decode
- * target, (5) per decode class (wavelet and 1 + tlevels coefficient
- * frames) one
- * persistent tile-decode launch over every coarse tile (levels L..3), then
- * every output tile (levels 2..1) of its targets, and (6) the reprojection
- * of every request.  Unfoveated requests of the same stream and frame share
- * one decode target, so a tile several of them need is decoded once.  The
+/* Decode n requests as one batch: one CUDA graph of the upload of the job
+ * tables from pinned host memory and the clearing of the counters, then per
+ * wave of decode targets (1) clearing of the wave's stamps, (2) the
+ * footprint of every request of the wave, (3) the tile lists of every decode
+ * target of the wave, (4) per decode class (wavelet and 1 + tlevels
+ * coefficient frames) one persistent tile-decode launch over every coarse
+ * tile (levels L..3), then every output tile (levels 2..1) of its targets,
+ * and (5) the reprojection of every request of the wave.  Unfoveated
+ * requests of the same stream and frame share one decode target, so a tile
+ * several of them need is decoded once; a foveated request (Sec. 3.7) has
+ * its own.  Targets are grouped into waves in request order.  The
  * graph is reused while the batch keeps its shape; the call returns before
  * the GPU finishes (outputs valid once the context's CUDA stream is
  * synchronised).  The streams and output images must stay alive until then;
@@ -302,18 +309,35 @@ int wv_batch_set_wait_limit(wv_batch *b, int polls);
 void wv_debug_fail_device_allocs(int n);
 
 /* on = 1: run batches as direct launches with CUDA events between the steps
- * (wv_batch_stats reports per-step times); on = 0: CUDA graph (default). */
+ * (wv_batch_stats reports per-step times, wv_batch_completion_ms the time
+ * each request completed); on = 0: CUDA graph (default). */
 int wv_batch_set_timing(wv_batch *b, int on);
 
-/* Tile shapes: output tile side (64 or 128 samples) and coarse tile side (32
- * or 64 samples of LL_2) for streams with this wavelet, level count and luma
- * size.  Default 128 / 64.  wv_batch_autotune times each of the four shapes
- * on the given requests (reps timed launches after one warm-up per shape, one
- * (wavelet, levels, size) class at a time) and keeps the fastest. */
+/* With timing on: the completion time of each of the last batch's n
+ * requests (caller order), in milliseconds from the start of the batch (the
+ * end of the reprojection of its wave).  Waits for the batch.  WV_ERR_ARG
+ * when timing was off or n differs from the batch's request count. */
+int wv_batch_completion_ms(wv_batch *b, double *ms, int n);
+
+/* Device bytes of decode targets one wave may hold (reconstruction and LL_2
+ * planes, stamps, list entries and foveation bits of its targets); a target
+ * larger than the limit forms a wave of its own.  Default 1 GiB; 0 = a
+ * single wave.  Outputs do not depend on it.  Takes effect from the next
+ * wv_batch_decode. */
+int wv_batch_set_memory_limit(wv_batch *b, size_t bytes);
+
+/* Tile shapes: output tile tile_w x tile_h samples (64 x 64, 128 x 128,
+ * 256 x 64 or 256 x 128) and coarse tile side (32 or 64 samples of LL_2) for
+ * streams with this wavelet, level count and luma size.  Default 128 x 128 /
+ * 64.  wv_batch_autotune times the shapes 128 x 128 / 64, 128 x 128 / 32,
+ * 64 x 64 / 64, 64 x 64 / 32, 256 x 64 / 64 and 256 x 128 / 64 on the given
+ * requests (reps timed launches after one warm-up per shape, one (wavelet,
+ * levels, size) class at a time) and keeps the fastest.  WV_ERR_ARG for
+ * other shapes. */
 int wv_batch_set_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height,
-                            int tile, int ctile);
-int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile,
-                        int *ctile);
+                            int tile_w, int tile_h, int ctile);
+int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile_w,
+                        int *tile_h, int *ctile);
 int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps);
 
 /* ---------------------------------------------------------------------------

@@ -203,9 +203,13 @@ cudaError_t launch_fine(wv_stream *s, const Bands &b, const float *const *ll2, u
                         float *f32, int f32_plane, const uint32_t *tiles, int *counters,
                         cudaStream_t cs) {
     const Geom &g = active_geom(s);
-    if (strip_mode(s))
-        return launch_decode_strips(g, s->payload, s->table, b, ll2, s->ll2_pitch, out_u8, f32, f32_plane, tiles,
-                                    counters, s->err, cs);
+    if (strip_mode(s)) {
+        // into the stream's reconstruction planes: chroma in alternating Cb, Cr groups
+        const bool pairs = out_u8[1] == s->recon[1] && out_u8[2] == s->recon[2] && recon_pairs(s);
+        uint8_t *const outs[3] = {out_u8[0], out_u8[1], pairs ? out_u8[1] + 4 : out_u8[2]};
+        return launch_decode_strips(g, s->payload, s->table, b, ll2, s->ll2_pitch, outs, f32, f32_plane, tiles,
+                                    counters, s->err, cs, pairs);
+    }
     return launch_decode_fine(g, s->payload, s->table, b, ll2, s->ll2_pitch, out_u8, f32, f32_plane, tiles,
                               counters, s->err, cs);
 }
@@ -345,7 +349,8 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     if (rc != WV_OK) return rc;
     const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, rows, row0);
     prof_begin(s, kKResample);
-    launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
+    launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr, nullptr,
+                    nullptr, recon_pairs(s));
     prof_end(s);
     return cuda_err(cudaGetLastError());
 }
@@ -483,6 +488,8 @@ cudaError_t opt_in_smem(const void *fn, int bytes) {
     return e;
 }
 
+bool recon_pairs(const wv_stream *s) { return s->pair_ok && s->decode_mode == 0 && s->g.strip; }
+
 namespace {
 
 // Common geometry of both tile organisations: output tiles tw x th (plane
@@ -578,6 +585,14 @@ int build_geom(const wv_stream_desc &d, Geom *g, int tile, int ctile) {
         return WV_ERR_ARG;
     }
     return build_geom_tiles(d, g, tile, tile, 0, ctile);
+}
+
+int build_geom_rect(const wv_stream_desc &d, Geom *g, int tw, int th, int ctile) {
+    if (tw < 64 || tw > 256 || th < 64 || th > 256) {
+        memset(g, 0, sizeof(*g));
+        return WV_ERR_ARG;
+    }
+    return build_geom_tiles(d, g, tw, th, 0, ctile);
 }
 
 // The strip kernel decodes levels 2 and 1 of dead-zone streams (LL_2 from the
@@ -778,6 +793,7 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
     if (!host_payload) s->payload = (int16_t *)(base + L.payload);
     s->table = (int32_t *)(base + L.table);
     for (int p = 0; p < 3; ++p) s->recon[p] = p < s->g.planes ? (uint8_t *)(base + L.recon[p]) : nullptr;
+    s->pair_ok = s->g.planes == 3 && L.recon[2] == L.recon[1] + (size_t)s->g.p[1].w * s->g.p[1].h;
     s->mask = (uint8_t *)(base + L.mask);
     s->tiles = (uint32_t *)(base + L.tiles);
     s->ctiles = (uint32_t *)(base + L.ctiles);
@@ -936,7 +952,8 @@ int wv_debug_project(wv_stream *s, float yaw, float pitch, float fov, int out_w,
 int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
     if (!s || !uv_dev || check_image(out) != WV_OK) return WV_ERR_ARG;
     View v = make_view(0.f, 0.f, 1.f, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
-    launch_resample(s->g, v, s->recon, uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs);
+    launch_resample(s->g, v, s->recon, uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr, nullptr,
+                    nullptr, recon_pairs(s));
     return cuda_err(cudaGetLastError());
 }
 

@@ -1,25 +1,32 @@
 // batch.cu -- batched viewport decoding: many requests over several streams
 // of uneven size, field of view and foveation in one CUDA graph.
 //
-// One batch is one graph of six steps on the batch's CUDA stream:
-//   1. upload of the job tables (one copy from pinned host memory);
-//   2. clearing of the tile stamps and work counters;
-//   3. footprint of every request (k_footprint_batch, one grid slice each);
-//   4. tile lists of every decode target (k_select_batch);
-//   5. per decode class (wavelet, number of coefficient frames the
+// One batch is one graph on the batch's CUDA stream: the upload of the job
+// tables (one copy from pinned host memory) and the clearing of the work
+// counters, then per wave of decode targets:
+//   1. clearing of the wave's tile stamps;
+//   2. footprint of every request of the wave (k_footprint_batch, one grid
+//      slice each);
+//   3. tile lists of every decode target of the wave (k_select_batch);
+//   4. per decode class (wavelet, number of coefficient frames the
 //      inter-frame rebuild reads) one persistent tile-decode launch over all
 //      coarse, then all fine tiles of its targets (k_tiles_batch);
-//   6. reprojection of every request (k_resample_batch).
+//   5. reprojection of every request of the wave (k_resample_batch).
 // Requests of the same stream and frame without foveation share one decode
 // target ("surface"), so a tile that several viewports need is decoded once.
 // A foveated request (Sec. 3.7) has a surface of its own, since the details
-// it drops depend on its gaze.  The instantiated graph is kept and relaunched
-// while the batch keeps its shape (counts, sizes, arena); between launches
-// only the job tables change.
+// it drops depend on its gaze.  Surfaces are grouped, in request order, into
+// waves whose planes fit the context's memory limit; every wave reuses the
+// same device region, so the arena stays bounded however many requests a
+// batch holds, and the requests of an early wave are complete before the
+// later waves run.  The instantiated graph is kept and relaunched while the
+// batch keeps its shape (counts, sizes, arena); between launches only the
+// job tables change.
 //
-// Tile shapes (output tile 64 or 128 samples, coarse tile 32 or 64 samples
-// of LL_2) are chosen per (wavelet, levels, frame size) by an autotuner that
-// times the batch with each shape (wv_batch_autotune).
+// Tile shapes (output tiles 64 x 64, 128 x 128, 256 x 64 or 256 x 128
+// samples, coarse tile 32 or 64 samples of LL_2) are chosen per (wavelet,
+// levels, frame size) by an autotuner that times the batch with each shape
+// (wv_batch_autotune).
 #include <math.h>
 #include <string.h>
 
@@ -40,27 +47,53 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 using TuneKey = std::array<int, 4>;   // wavelet, levels, width, height
 
+struct Shape {
+    int tw, th, ctile;   // output tile (plane samples), coarse tile (LL_2 samples)
+    bool operator==(const Shape &o) const { return tw == o.tw && th == o.th && ctile == o.ctile; }
+};
+constexpr Shape kDefaultShape = {kTile, kTile, kCoarseTile};
+// Output tiles the batch decoder takes: the fine pass's shared arrays of a
+// 256 x 128 tile (levels 2 and 1, 9/7) are about 174 KB, of 256 x 256 about
+// 340 KB (too large).
+bool shape_ok(int tw, int th, int ctile) {
+    const bool out = (tw == 64 && th == 64) || (tw == 128 && th == 128) || (tw == 256 && (th == 64 || th == 128));
+    return out && (ctile == 32 || ctile == 64);
+}
+
 struct Surface {
     wv_stream *s;
     int frame;
     bool foveated;
     Geom g;
     int cls;
-    size_t recon[3], ll2[3], fmask, stamp;
+    int wave;
+    size_t bytes;   // device bytes of its stamps, list entries and planes
+    size_t recon[3], ll2[3], fmask, stamp;   // arena offsets (inside the wave region)
 };
 
 // Arena word holding the bounded wait's poll limit (inside the 256 bytes
 // before the job tables; the error word is at offset 0).
 constexpr size_t kWaitWord = 64;
 
+// A wave: surfaces [s0, s1) and the rows [r0, r1) of the request table (the
+// table lists requests by wave, in caller order inside a wave).
+struct Wave {
+    int s0, s1, r0, r1;
+    size_t ctr;            // its counters (kBatchCtr + 2 (s1 - s0) ints)
+    size_t stamps, stamp_bytes;
+    size_t lists_c[kClasses], lists_f[kClasses];
+    int smem[kClasses];    // dynamic shared memory of each class's decode (0: class absent)
+    int max_cx, max_cy, max_stamps, max_w, max_h;
+};
+
 struct Plan {
     std::vector<Surface> surf;
-    std::vector<int> req_surface;
-    size_t jobs, reqs, ctr, stamps, lists_c[kClasses], lists_f[kClasses], err, total;
-    size_t clear_bytes;   // counters + stamps, cleared every launch
+    std::vector<int> req_surface;   // per request (caller order)
+    std::vector<int> order;         // request table row -> request index
+    std::vector<Wave> waves;
+    size_t err, jobs, reqs, ctr, region, total;
+    size_t ctr_bytes;               // counters of all waves, cleared every launch
     int n_ctr;
-    int max_cx, max_cy, max_stamps, max_w, max_h;
-    int smem[kClasses];   // dynamic shared memory of each class's decode (0: class absent)
     size_t job_bytes;
 };
 
@@ -80,17 +113,22 @@ struct wv_batch {
     bool use_graph = true;
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> shape;      // key of the instantiated graph
-    std::map<TuneKey, std::pair<int, int>> tuned;
+    std::map<TuneKey, Shape> tuned;
     int *err = nullptr;
     // statistics of the last launch (read back on request)
     int last_requests = 0, last_surfaces = 0;
     int *ctr_dev = nullptr;
     int n_ctr = 0;
-    // per-step timing of the last launch (direct mode only)
+    std::vector<int> ctr_base;         // first counter of each wave of the last launch
+    std::vector<int> req_wave;         // wave of each request of the last launch
+    // per-step timing of the last launch (direct mode only): a start event,
+    // then 5 per wave (after the stamp clear, footprint, lists, decode,
+    // reprojection)
     bool timing = false;
-    cudaEvent_t ev[5] = {};
+    std::vector<cudaEvent_t> ev;
     bool share = true;                 // unfoveated requests of one (stream, frame) share a surface
     int wait_polls = kBatchWaitPolls;  // polls of the tile decode's bounded wait (arena word at kWaitWord)
+    size_t wave_bytes = kBatchWaveBytes;   // device bytes of one wave's surfaces (0: one wave)
 };
 
 namespace {
@@ -112,14 +150,28 @@ int check_request(const wv_request &r) {
     return WV_OK;
 }
 
-std::pair<int, int> tile_shape(const wv_batch *b, const Geom &g) {
+Shape tile_shape(const wv_batch *b, const Geom &g) {
     auto it = b->tuned.find(TuneKey{g.wavelet, g.levels, g.p[0].w, g.p[0].h});
-    return it == b->tuned.end() ? std::make_pair(kTile, kCoarseTile) : it->second;
+    return it == b->tuned.end() ? kDefaultShape : it->second;
+}
+
+// Device bytes of a surface's own data: stamps, worst-case list entries,
+// reconstruction and LL_2 planes, foveation cell bits (each 256-aligned).
+size_t surface_bytes(const Surface &S) {
+    size_t o = sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
+    o += sizeof(uint2) * (S.g.total_tiles + S.g.total_ctiles) + 512;
+    for (int p = 0; p < S.g.planes; ++p) {
+        o += align256((size_t)S.g.p[p].w * S.g.p[p].h);
+        if (S.g.levels >= 3) o += align256((size_t)S.g.p[p].ll2_pitch * (S.g.p[p].h >> 2) * 4);
+    }
+    if (S.foveated) o += align256((size_t)S.g.cells_x * S.g.cells_y);
+    return o;
 }
 
 int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
     std::map<std::pair<const wv_stream *, int>, int> shared;
     P.surf.clear();
+    P.waves.clear();
     P.req_surface.assign(n, -1);
     for (int i = 0; i < n; ++i) {
         const wv_request &r = reqs[i];
@@ -135,19 +187,45 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         S.frame = r.frame;
         S.foveated = r.fovea != 0;
         const Geom &sg = r.s->g;
-        const std::pair<int, int> ts = tile_shape(b, sg);
-        if (build_geom(r.s->desc, &S.g, ts.first, ts.second) != WV_OK) return WV_ERR_ARG;
+        const Shape ts = tile_shape(b, sg);
+        if (build_geom_rect(r.s->desc, &S.g, ts.tw, ts.th, ts.ctile) != WV_OK) return WV_ERR_ARG;
         S.g.dz_t = sg.dz_t;   // the code form of the stream's device payload
         // 1 + tlevels coefficient frames
         const int group = S.g.dz_t ? 4 + (S.foveated ? 1 : 0) : 2 * S.g.wavelet + (S.foveated ? 1 : 0);
         S.cls = kMaxBands * group + S.g.tlevels;
+        S.bytes = surface_bytes(S);
         P.req_surface[i] = (int)P.surf.size();
         if (!r.fovea) shared[{r.s, r.frame}] = (int)P.surf.size();
         P.surf.push_back(S);
     }
     const int m = (int)P.surf.size();
-    // arena: error word | job tables | counters | stamps | lists | per-surface
-    // planes.  The error word stays at offset 0 for every plan.
+    // waves: surfaces in order while their bytes fit the limit (a surface
+    // larger than the limit forms a wave of its own)
+    {
+        size_t acc = 0;
+        int s0 = 0;
+        for (int i = 0; i < m; ++i) {
+            if (i > s0 && b->wave_bytes && acc + P.surf[i].bytes > b->wave_bytes) {
+                P.waves.push_back(Wave{s0, i});
+                s0 = i;
+                acc = 0;
+            }
+            acc += P.surf[i].bytes;
+            P.surf[i].wave = (int)P.waves.size();
+        }
+        if (m > 0) P.waves.push_back(Wave{s0, m});
+    }
+    // request table: by wave, caller order inside a wave
+    P.order.clear();
+    for (Wave &W : P.waves) {
+        W.r0 = (int)P.order.size();
+        for (int i = 0; i < n; ++i)
+            if (P.req_surface[i] >= W.s0 && P.req_surface[i] < W.s1) P.order.push_back(i);
+        W.r1 = (int)P.order.size();
+    }
+    // arena: error word | job tables | counters of every wave | wave region
+    // (stamps | lists | per-surface planes, reused by every wave).  The error
+    // word stays at offset 0 for every plan.
     P.err = 0;
     size_t o = 256;
     P.jobs = o;
@@ -156,48 +234,58 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
     o = align256(o + sizeof(RequestJob) * n);
     P.job_bytes = o;
     P.ctr = o;
-    P.n_ctr = kBatchCtr + 2 * m;
-    o += sizeof(int) * P.n_ctr;
-    P.stamps = o;
-    size_t tiles[kClasses] = {}, ctiles[kClasses] = {};
-    P.max_cx = P.max_cy = P.max_stamps = 0;
-    for (Surface &S : P.surf) {
-        S.stamp = o;
-        o += sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
-        tiles[S.cls] += S.g.total_tiles;
-        ctiles[S.cls] += S.g.total_ctiles;
-        P.max_cx = std::max(P.max_cx, S.g.cells_x);
-        P.max_cy = std::max(P.max_cy, S.g.cells_y);
-        P.max_stamps = std::max(P.max_stamps, S.g.total_tiles + S.g.total_ctiles);
+    P.n_ctr = 0;
+    for (Wave &W : P.waves) {
+        W.ctr = P.ctr + sizeof(int) * P.n_ctr;
+        P.n_ctr += kBatchCtr + 2 * (W.s1 - W.s0);
     }
-    P.clear_bytes = o - P.ctr;
-    o = align256(o);
-    for (int c = 0; c < kClasses; ++c) {
-        P.lists_c[c] = o;
-        o = align256(o + sizeof(uint2) * std::max<size_t>(ctiles[c], 1));
-        P.lists_f[c] = o;
-        o = align256(o + sizeof(uint2) * std::max<size_t>(tiles[c], 1));
-    }
-    for (Surface &S : P.surf) {
-        for (int p = 0; p < 3; ++p) {
-            S.recon[p] = o;
-            if (p < S.g.planes) o = align256(o + (size_t)S.g.p[p].w * S.g.p[p].h);
+    P.ctr_bytes = sizeof(int) * P.n_ctr;
+    P.region = align256(P.ctr + P.ctr_bytes);
+    P.total = P.region;
+    for (Wave &W : P.waves) {
+        o = P.region;
+        W.stamps = o;
+        size_t tiles[kClasses] = {}, ctiles[kClasses] = {};
+        W.max_cx = W.max_cy = W.max_stamps = W.max_w = W.max_h = 0;
+        for (int si = W.s0; si < W.s1; ++si) {
+            Surface &S = P.surf[si];
+            S.stamp = o;
+            o += sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
+            tiles[S.cls] += S.g.total_tiles;
+            ctiles[S.cls] += S.g.total_ctiles;
+            W.max_cx = std::max(W.max_cx, S.g.cells_x);
+            W.max_cy = std::max(W.max_cy, S.g.cells_y);
+            W.max_stamps = std::max(W.max_stamps, S.g.total_tiles + S.g.total_ctiles);
         }
-        for (int p = 0; p < 3; ++p) {
-            S.ll2[p] = o;
-            if (p < S.g.planes && S.g.levels >= 3)
-                o = align256(o + (size_t)S.g.p[p].ll2_pitch * (S.g.p[p].h >> 2) * 4);
+        W.stamp_bytes = o - W.stamps;
+        o = align256(o);
+        for (int c = 0; c < kClasses; ++c) {
+            W.lists_c[c] = o;
+            o = align256(o + sizeof(uint2) * std::max<size_t>(ctiles[c], 1));
+            W.lists_f[c] = o;
+            o = align256(o + sizeof(uint2) * std::max<size_t>(tiles[c], 1));
         }
-        S.fmask = o;
-        if (S.foveated) o = align256(o + (size_t)S.g.cells_x * S.g.cells_y);
+        for (int si = W.s0; si < W.s1; ++si) {
+            Surface &S = P.surf[si];
+            for (int p = 0; p < 3; ++p) {
+                S.recon[p] = o;
+                if (p < S.g.planes) o = align256(o + (size_t)S.g.p[p].w * S.g.p[p].h);
+            }
+            for (int p = 0; p < 3; ++p) {
+                S.ll2[p] = o;
+                if (p < S.g.planes && S.g.levels >= 3)
+                    o = align256(o + (size_t)S.g.p[p].ll2_pitch * (S.g.p[p].h >> 2) * 4);
+            }
+            S.fmask = o;
+            if (S.foveated) o = align256(o + (size_t)S.g.cells_x * S.g.cells_y);
+        }
+        P.total = std::max(P.total, o);
+        for (int k = W.r0; k < W.r1; ++k) {
+            W.max_w = std::max(W.max_w, reqs[P.order[k]].out.width);
+            W.max_h = std::max(W.max_h, reqs[P.order[k]].out.height);
+        }
+        for (int c = 0; c < kClasses; ++c) W.smem[c] = 0;
     }
-    P.total = o;
-    P.max_w = P.max_h = 0;
-    for (int i = 0; i < n; ++i) {
-        P.max_w = std::max(P.max_w, reqs[i].out.width);
-        P.max_h = std::max(P.max_h, reqs[i].out.height);
-    }
-    for (int c = 0; c < kClasses; ++c) P.smem[c] = 0;
     return WV_OK;
 }
 
@@ -255,10 +343,12 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         J.cls = S.cls;
         int need = (J.fine.a_floats + J.fine.p_floats) * 4;
         if (S.g.levels >= 3) need = std::max(need, (J.coarse.a_floats + J.coarse.p_floats) * 4);
-        P.smem[S.cls] = std::max(P.smem[S.cls], need);
+        int &sm = P.waves[S.wave].smem[S.cls];
+        sm = std::max(sm, need);
         memcpy(&sj[i], &J, sizeof(J));
     }
-    for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < n; ++k) {
+        const int i = P.order[k];
         const wv_request &r = reqs[i];
         const Surface &S = P.surf[P.req_surface[i]];
         RequestJob R;
@@ -272,7 +362,7 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         R.fov.gy = r.gaze_y;
         R.fov.r1 = r.r1;
         R.fov.r2 = r.r2;
-        R.surface = P.req_surface[i];
+        R.surface = P.req_surface[i] - P.waves[S.wave].s0;   // index within the wave
         R.rs.v = R.v;
         for (int p = 0; p < 3; ++p) {
             const bool has = p < S.g.planes;
@@ -285,62 +375,87 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         R.rs.uv = nullptr;
         R.rs.out = (uint8_t *)r.out.dptr;
         R.rs.pitch = r.out.pitch_bytes;
-        memcpy(&rj[i], &R, sizeof(R));
+        memcpy(&rj[k], &R, sizeof(R));
     }
 }
 
-// Enqueue the six steps on cs (captured into a graph, or run directly).
+// Enqueue the batch on cs (captured into a graph, or run directly with
+// events between the steps when timed).
 cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool timed) {
     char *base = b->dmem;
     const SurfaceJob *surfs = (const SurfaceJob *)(base + P.jobs);
     const RequestJob *rq = (const RequestJob *)(base + P.reqs);
-    int *ctr = (int *)(base + P.ctr);
-    const int m = (int)P.surf.size();
+    if (timed) cudaEventRecord(b->ev[0], cs);
     // the wait limit word, then the job tables (the error word at 0 stays)
     cudaError_t e = cudaMemcpyAsync(base + kWaitWord, b->host + kWaitWord, P.job_bytes - kWaitWord,
                                     cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return e;
-    e = timed ? cudaEventRecord(b->staged, cs) : cudaEventRecordWithFlags(b->staged, cs, cudaEventRecordExternal);
+    e = cs == b->cap ? cudaEventRecordWithFlags(b->staged, cs, cudaEventRecordExternal) : cudaEventRecord(b->staged, cs);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(base + P.ctr, 0, P.clear_bytes, cs);
+    e = cudaMemsetAsync(base + P.ctr, 0, P.ctr_bytes, cs);
     if (e != cudaSuccess) return e;
-    if (timed) cudaEventRecord(b->ev[0], cs);
-    launch_footprint_batch(rq, surfs, n, P.max_cx, P.max_cy, cs);
-    if (timed) cudaEventRecord(b->ev[1], cs);
-    BatchLists lists;
-    for (int c = 0; c < kClasses; ++c) {
-        lists.coarse[c] = (uint2 *)(base + P.lists_c[c]);
-        lists.fine[c] = (uint2 *)(base + P.lists_f[c]);
-    }
-    launch_select_batch(surfs, m, P.max_stamps, lists, ctr, cs);
-    if (timed) cudaEventRecord(b->ev[2], cs);
-    for (int c = 0; c < kClasses; ++c) {
-        if (!P.smem[c]) continue;
-        const int group = c / kMaxBands;
-        e = launch_decode_batch(group >= 4 ? WV_WAVELET_97 : group / 2, c % kMaxBands + 1, group % 2 == 1,
-                                group >= 4, surfs,
-                                lists.coarse[c], lists.fine[c], ctr + 4 * c,
-                                ctr + kBatchCtr, (int *)(base + P.err), (const int *)(base + kWaitWord), P.smem[c],
-                                cs);
+    for (size_t w = 0; w < P.waves.size(); ++w) {
+        const Wave &W = P.waves[w];
+        cudaEvent_t *ev = timed ? &b->ev[1 + 5 * w] : nullptr;
+        const int m = W.s1 - W.s0, nr = W.r1 - W.r0;
+        int *ctr = (int *)(base + W.ctr);
+        e = cudaMemsetAsync(base + W.stamps, 0, W.stamp_bytes, cs);
         if (e != cudaSuccess) return e;
+        if (timed) cudaEventRecord(ev[0], cs);
+        launch_footprint_batch(rq + W.r0, surfs + W.s0, nr, W.max_cx, W.max_cy, cs);
+        if (timed) cudaEventRecord(ev[1], cs);
+        BatchLists lists;
+        for (int c = 0; c < kClasses; ++c) {
+            lists.coarse[c] = (uint2 *)(base + W.lists_c[c]);
+            lists.fine[c] = (uint2 *)(base + W.lists_f[c]);
+        }
+        launch_select_batch(surfs + W.s0, m, W.max_stamps, lists, ctr, cs);
+        if (timed) cudaEventRecord(ev[2], cs);
+        for (int c = 0; c < kClasses; ++c) {
+            if (!W.smem[c]) continue;
+            const int group = c / kMaxBands;
+            e = launch_decode_batch(group >= 4 ? WV_WAVELET_97 : group / 2, c % kMaxBands + 1, group % 2 == 1,
+                                    group >= 4, surfs + W.s0, lists.coarse[c], lists.fine[c], ctr + 4 * c,
+                                    ctr + kBatchCtr, (int *)(base + P.err), (const int *)(base + kWaitWord),
+                                    W.smem[c], cs);
+            if (e != cudaSuccess) return e;
+        }
+        if (timed) cudaEventRecord(ev[3], cs);
+        launch_resample_batch(rq + W.r0, nr, W.max_w, W.max_h, cs);
+        if (timed) cudaEventRecord(ev[4], cs);
     }
-    if (timed) cudaEventRecord(b->ev[3], cs);
-    launch_resample_batch(rq, n, P.max_w, P.max_h, cs);
-    if (timed) cudaEventRecord(b->ev[4], cs);
     return cudaGetLastError();
 }
 
 std::vector<long long> shape_key(const wv_batch *b, const Plan &P, int n) {
     std::vector<long long> k = {n, (long long)P.surf.size(), (long long)(uintptr_t)b->dmem,
                                 (long long)(uintptr_t)b->host, (long long)P.job_bytes,
-                                (long long)P.clear_bytes, P.max_cx, P.max_cy, P.max_stamps,
-                                P.max_w, P.max_h};
-    for (int c = 0; c < kClasses; ++c) {
-        k.push_back(P.smem[c]);
-        k.push_back((long long)P.lists_c[c]);
-        k.push_back((long long)P.lists_f[c]);
+                                (long long)P.ctr_bytes, (long long)P.waves.size()};
+    for (const Wave &W : P.waves) {
+        for (long long v : {(long long)W.s0, (long long)W.s1, (long long)W.r0, (long long)W.r1, (long long)W.ctr,
+                            (long long)W.stamps, (long long)W.stamp_bytes, (long long)W.max_cx,
+                            (long long)W.max_cy, (long long)W.max_stamps, (long long)W.max_w, (long long)W.max_h})
+            k.push_back(v);
+        for (int c = 0; c < kClasses; ++c) {
+            k.push_back(W.smem[c]);
+            k.push_back((long long)W.lists_c[c]);
+            k.push_back((long long)W.lists_f[c]);
+        }
     }
     return k;
+}
+
+// Events of a timed launch: one start event and five per wave.
+int ensure_events(wv_batch *b, size_t waves) {
+    while (b->ev.size() < 1 + 5 * waves) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return WV_ERR_CUDA;
+        }
+        b->ev.push_back(e);
+    }
+    return WV_OK;
 }
 
 int ensure_memory(wv_batch *b, const Plan &P) {
@@ -384,6 +499,7 @@ int run_batch(wv_batch *b, const wv_request *reqs, int n, cudaStream_t cs) {
     if (rc != WV_OK) return rc;
     rc = ensure_memory(b, P);
     if (rc != WV_OK) return rc;
+    if (b->timing && (rc = ensure_events(b, P.waves.size())) != WV_OK) return rc;
     // the previous launch must have consumed the staging before it is rewritten
     if (b->launched) cudaEventSynchronize(b->staged);
     fill_jobs(b, reqs, n, P);
@@ -394,6 +510,10 @@ int run_batch(wv_batch *b, const wv_request *reqs, int n, cudaStream_t cs) {
     b->n_ctr = P.n_ctr;
     b->last_requests = n;
     b->last_surfaces = (int)P.surf.size();
+    b->ctr_base.clear();
+    for (const Wave &W : P.waves) b->ctr_base.push_back((int)((W.ctr - P.ctr) / sizeof(int)));
+    b->req_wave.assign(n, 0);
+    for (int i = 0; i < n; ++i) b->req_wave[i] = P.surf[P.req_surface[i]].wave;
     cudaError_t e;
     if (b->use_graph && !b->timing) {
         const std::vector<long long> key = shape_key(b, P, n);
@@ -418,7 +538,7 @@ int run_batch(wv_batch *b, const wv_request *reqs, int n, cudaStream_t cs) {
         }
         e = cudaGraphLaunch(b->exec, cs);
     } else {
-        e = enqueue(b, P, n, cs, true);
+        e = enqueue(b, P, n, cs, b->timing);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, cs);
     if (e != cudaSuccess) {
@@ -460,7 +580,6 @@ int wv_batch_create(void *cuda_stream, wv_batch **out) {
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         wv_batch_close(b);
@@ -528,18 +647,40 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info) {
         return WV_ERR_CUDA;
     info->requests = b->last_requests;
     info->surfaces = b->last_surfaces;
-    for (int k = 0; k < kClasses; ++k) {
-        info->coarse_tiles += c[4 * k + 1];
-        info->fine_tiles += c[4 * k + 2];
-    }
+    info->waves = (int)b->ctr_base.size();
+    for (int c0 : b->ctr_base)
+        for (int k = 0; k < kClasses; ++k) {
+            info->coarse_tiles += c[c0 + 4 * k + 1];
+            info->fine_tiles += c[c0 + 4 * k + 2];
+        }
     info->bytes = b->dbytes;
     if (b->timing) {
         float ms = 0.f;
-        for (int i = 0; i < 4; ++i) {
-            cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]);
-            info->ms[i] = ms;
-        }
+        for (size_t w = 0; w < b->ctr_base.size(); ++w)
+            for (int i = 0; i < 4; ++i) {
+                cudaEventElapsedTime(&ms, b->ev[1 + 5 * w + i], b->ev[1 + 5 * w + i + 1]);
+                info->ms[i] += ms;
+            }
     }
+    return WV_OK;
+}
+
+int wv_batch_completion_ms(wv_batch *b, double *ms, int n) {
+    if (!b || !ms || n < 0) return WV_ERR_ARG;
+    if (!b->launched || !b->timing || n != b->last_requests || b->ev.size() < 1 + 5 * b->ctr_base.size())
+        return WV_ERR_ARG;
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return WV_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, b->ev[0], b->ev[1 + 5 * b->req_wave[i] + 4]) != cudaSuccess) return WV_ERR_CUDA;
+        ms[i] = t;
+    }
+    return WV_OK;
+}
+
+int wv_batch_set_memory_limit(wv_batch *b, size_t bytes) {
+    if (!b) return WV_ERR_ARG;
+    b->wave_bytes = bytes;
     return WV_OK;
 }
 
@@ -562,18 +703,20 @@ int wv_batch_set_timing(wv_batch *b, int on) {
 }
 
 int wv_batch_set_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height,
-                            int tile, int ctile) {
-    if (!b || (tile != 64 && tile != 128) || (ctile != 32 && ctile != 64)) return WV_ERR_ARG;
-    b->tuned[TuneKey{wavelet, levels, width, height}] = {tile, ctile};
+                            int tile_w, int tile_h, int ctile) {
+    if (!b || !shape_ok(tile_w, tile_h, ctile)) return WV_ERR_ARG;
+    b->tuned[TuneKey{wavelet, levels, width, height}] = Shape{tile_w, tile_h, ctile};
     return WV_OK;
 }
 
-int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile,
-                        int *ctile) {
-    if (!b || !tile || !ctile) return WV_ERR_ARG;
+int wv_batch_tile_shape(wv_batch *b, int wavelet, int levels, int width, int height, int *tile_w,
+                        int *tile_h, int *ctile) {
+    if (!b || !tile_w || !tile_h || !ctile) return WV_ERR_ARG;
     auto it = b->tuned.find(TuneKey{wavelet, levels, width, height});
-    *tile = it == b->tuned.end() ? kTile : it->second.first;
-    *ctile = it == b->tuned.end() ? kCoarseTile : it->second.second;
+    const Shape sh = it == b->tuned.end() ? kDefaultShape : it->second;
+    *tile_w = sh.tw;
+    *tile_h = sh.th;
+    *ctile = sh.ctile;
     return WV_OK;
 }
 
@@ -586,7 +729,7 @@ int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps) {
         const TuneKey k{g.wavelet, g.levels, g.p[0].w, g.p[0].h};
         if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
     }
-    const std::pair<int, int> cand[4] = {{128, 64}, {128, 32}, {64, 64}, {64, 32}};
+    const Shape cand[] = {{128, 128, 64}, {128, 128, 32}, {64, 64, 64}, {64, 64, 32}, {256, 64, 64}, {256, 128, 64}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WV_ERR_CUDA;
     int rc = WV_OK;
@@ -594,7 +737,7 @@ int wv_batch_autotune(wv_batch *b, const wv_request *reqs, int n, int reps) {
     b->timing = false;
     for (const TuneKey &k : keys) {
         float best = 1e30f;
-        std::pair<int, int> pick = cand[0];
+        Shape pick = cand[0];
         for (const auto &c : cand) {
             b->tuned[k] = c;
             rc = run_batch(b, reqs, n, b->cs);   // warm-up (captures the graph)

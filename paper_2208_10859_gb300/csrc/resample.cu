@@ -28,10 +28,24 @@ struct Taps {
     int fx, fy;
 };
 
+// fixed_split for |t| < 2^15 (every projected position): there t * 256 +
+// 1/2 is exact in float32, so floor(t * 256 + 1/2) = 256 i + f, the carry
+// included, and one rounding conversion gives both parts.
+__device__ __forceinline__ void fixed_split_near(float t, int &i, int &f) {
+    const int T = __float2int_rd(fmaf(t, 256.0f, 0.5f));
+    i = T >> 8;
+    f = T & 255;
+}
+
 __device__ __forceinline__ Taps bilinear_taps(int w, int r_lo, int r_n, float u, float v) {
     int x0, fx, y0, fy;
-    fixed_split(u, x0, fx);
-    fixed_split(v, y0, fy);
+    if (fabsf(u) < 32768.0f && fabsf(v) < 32768.0f) {
+        fixed_split_near(u, x0, fx);
+        fixed_split_near(v, y0, fy);
+    } else {
+        fixed_split(u, x0, fx);
+        fixed_split(v, y0, fy);
+    }
     Taps t;
     t.fx = fx;
     t.fy = fy;
@@ -67,6 +81,26 @@ __device__ __forceinline__ int blend(const uint8_t *__restrict__ img, const Taps
     return ((256 - t.fy) * top + t.fy * bot + 32768) >> 16;
 }
 
+// Cb and Cr of chroma sample e (row-major index) from a plane of
+// alternating 4-sample groups (Cb of positions 4k..4k+3, then Cr of the
+// same positions): one 8-byte load.
+__device__ __forceinline__ uint2 tap_pair(const uint8_t *__restrict__ img, int e) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(img + 2 * (e & ~3)));
+    const int sh = 8 * (e & 3);
+    return make_uint2((q.x >> sh) & 255u, (q.y >> sh) & 255u);
+}
+
+// Cb and Cr of one tap set: four 8-byte loads instead of eight byte loads.
+__device__ __forceinline__ void blend_pair(const uint8_t *__restrict__ img, const Taps &t, int &cb, int &cr) {
+    const uint2 p00 = tap_pair(img, t.a0), p01 = tap_pair(img, t.a1);
+    const uint2 p10 = tap_pair(img, t.b0), p11 = tap_pair(img, t.b1);
+    const int wx1 = t.fx, wx0 = 256 - t.fx;
+    const int tb = wx0 * (int)p00.x + wx1 * (int)p01.x, bb = wx0 * (int)p10.x + wx1 * (int)p11.x;
+    const int tr = wx0 * (int)p00.y + wx1 * (int)p01.y, br = wx0 * (int)p10.y + wx1 * (int)p11.y;
+    cb = ((256 - t.fy) * tb + t.fy * bb + 32768) >> 16;
+    cr = ((256 - t.fy) * tr + t.fy * br + 32768) >> 16;
+}
+
 // Y, Cb, Cr of luma position (u, v); Cb and Cr share their taps.  Rows
 // clamp to the eye's part of the frame (all of it for mono streams).
 __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, float v, int &y, int &cb,
@@ -81,8 +115,12 @@ __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, flo
         }
         const int sh = a.c420 ? 1 : 0;
         const Taps t = bilinear_taps(a.w[1], a.v.row0 >> sh, a.v.rows >> sh, uc, vc);
-        cb = blend(a.plane[1], t);
-        cr = blend(a.plane[2], t);
+        if (a.c_pair) {
+            blend_pair(a.plane[1], t, cb, cr);
+        } else {
+            cb = blend(a.plane[1], t);
+            cr = blend(a.plane[2], t);
+        }
     }
 }
 
@@ -104,65 +142,68 @@ __device__ __forceinline__ void sample_ycc(const ResampleArgs &a, int i, int j) 
     a.cr_plane[o] = (uint8_t)cr;
 }
 
-// Two horizontally adjacent pixels (i, j), (i + 1, j) per thread
-// (independent work for the scheduler to overlap), written with one 8-byte
-// store when aligned.
-__device__ __forceinline__ void resample_pair(const ResampleArgs &a, int i, int j) {
+__device__ __forceinline__ uint32_t rgba_word(uchar4 c) {
+    return (uint32_t)c.x | ((uint32_t)c.y << 8) | ((uint32_t)c.z << 16) | ((uint32_t)c.w << 24);
+}
+
+__device__ __forceinline__ void position(const ResampleArgs &a, int i, int j, float &u, float &v) {
+    if (a.uv) {
+        const float2 p = reinterpret_cast<const float2 *>(a.uv)[(size_t)j * a.v.out_w + i];
+        u = p.x;
+        v = p.y;
+    } else {
+        project_px(a.v, i, j, u, v);
+    }
+}
+
+// kPx horizontally adjacent pixels (i .. i + kPx - 1, j) per thread
+// (independent work for the scheduler to overlap), written with one
+// 4 kPx-byte store when the row holds all of them and the address is
+// aligned.
+constexpr int kPx = 2;
+
+__device__ __forceinline__ void resample_run(const ResampleArgs &a, int i, int j) {
     if (i >= a.v.out_w || j >= a.v.out_h) return;
     if (a.y_plane) {
-        sample_ycc(a, i, j);
-        if (i + 1 < a.v.out_w) sample_ycc(a, i + 1, j);
+        for (int k = 0; k < kPx && i + k < a.v.out_w; ++k) sample_ycc(a, i + k, j);
         return;
     }
-    const bool two = i + 1 < a.v.out_w;
-    float u0, v0, u1 = 0.f, v1 = 0.f;
-    if (a.uv) {
-        const float2 *row = reinterpret_cast<const float2 *>(a.uv) + (size_t)j * a.v.out_w;
-        const float2 p0 = row[i];
-        u0 = p0.x;
-        v0 = p0.y;
-        if (two) {
-            const float2 p1 = row[i + 1];
-            u1 = p1.x;
-            v1 = p1.y;
-        }
-    } else {
-        project_px(a.v, i, j, u0, v0);
-        if (two) project_px(a.v, i + 1, j, u1, v1);
-    }
-    const uchar4 c0 = sample_px(a, u0, v0);
     uchar4 *dst = reinterpret_cast<uchar4 *>(a.out + (size_t)j * a.pitch) + i;
-    if (two) {
-        const uchar4 c1 = sample_px(a, u1, v1);
-        if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
-            uint2 w;
-            w.x = (uint32_t)c0.x | ((uint32_t)c0.y << 8) | ((uint32_t)c0.z << 16) | ((uint32_t)c0.w << 24);
-            w.y = (uint32_t)c1.x | ((uint32_t)c1.y << 8) | ((uint32_t)c1.z << 16) | ((uint32_t)c1.w << 24);
-            *reinterpret_cast<uint2 *>(dst) = w;
-        } else {
-            dst[0] = c0;
-            dst[1] = c1;
+    if (i + kPx <= a.v.out_w && (reinterpret_cast<uintptr_t>(dst) & (4 * kPx - 1)) == 0) {
+        uint32_t w[kPx];
+#pragma unroll
+        for (int k = 0; k < kPx; ++k) {
+            float u, v;
+            position(a, i + k, j, u, v);
+            w[k] = rgba_word(sample_px(a, u, v));
         }
-    } else {
-        dst[0] = c0;
+        if constexpr (kPx == 4) *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        else if constexpr (kPx == 2) *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<uint32_t *>(dst) = w[0];
+        return;
+    }
+    for (int k = 0; k < kPx && i + k < a.v.out_w; ++k) {
+        float u, v;
+        position(a, i + k, j, u, v);
+        dst[k] = sample_px(a, u, v);
     }
 }
 
 __global__ void k_resample(ResampleArgs a) {
-    resample_pair(a, 2 * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
+    resample_run(a, kPx * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // Batch: one z-slice of the grid per request.
 __global__ void k_resample_batch(const RequestJob *__restrict__ reqs) {
     const ResampleArgs &a = reqs[blockIdx.z].rs;
-    resample_pair(a, 2 * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
+    resample_run(a, kPx * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 }  // namespace
 
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane,
-                     uint8_t *cb_plane, uint8_t *cr_plane) {
+                     uint8_t *cb_plane, uint8_t *cr_plane, bool c_pair) {
     ResampleArgs a;
     memset(&a, 0, sizeof(a));
     a.y_plane = y_plane;
@@ -176,17 +217,18 @@ void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const 
     }
     a.planes = g.planes;
     a.c420 = g.c420;
+    a.c_pair = c_pair && g.planes == 3 ? 1 : 0;
     a.uv = uv;
     a.out = out;
     a.pitch = pitch;
     dim3 block(32, 8);
-    dim3 grid((v.out_w + 63) / 64, (v.out_h + 7) / 8);
+    dim3 grid((v.out_w + 32 * kPx - 1) / (32 * kPx), (v.out_h + 7) / 8);
     k_resample<<<grid, block, 0, cs>>>(a);
 }
 
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs) {
     dim3 block(32, 8);
-    dim3 grid((max_w + 63) / 64, (max_h + 7) / 8, n);
+    dim3 grid((max_w + 32 * kPx - 1) / (32 * kPx), (max_h + 7) / 8, n);
     k_resample_batch<<<grid, block, 0, cs>>>(reqs);
 }
 

@@ -532,6 +532,7 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
     const bool writer = lane >= 1 && lane <= 28 && (!EDGE || l1.c0 + 8 <= W);
     const bool to_f32 = a.out_f32 && plane == a.f32_plane;
     uint8_t *out8 = a.out_u8[plane];
+    const int pair_sh = a.out_pair && plane > 0 ? 1 : 0;
 
     SubRow<NB> r2[4], r1[4];
 #pragma unroll
@@ -719,10 +720,11 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                                 if constexpr (WAV == 1) p[m] = __float2int_rd(v[m] + 128.5f);
                                 else p[m] = v[m] + 128;
                             }
-                            uint2 pk;
-                            pk.x = pack4_sat(p[0], p[1], p[2], p[3]);
-                            pk.y = pack4_sat(p[4], p[5], p[6], p[7]);
-                            *reinterpret_cast<uint2 *>(out8 + o) = pk;
+                            // two groups of 4 samples: adjacent, or (chroma groups)
+                            // with the other chroma plane's group between them
+                            uint32_t *d = reinterpret_cast<uint32_t *>(out8 + (o << pair_sh));
+                            d[0] = pack4_sat(p[0], p[1], p[2], p[3]);
+                            d[1 << pair_sh] = pack4_sat(p[4], p[5], p[6], p[7]);
                         }
                     }
                 }
@@ -791,7 +793,10 @@ cudaError_t launch_nb(const TileArgs &a, cudaStream_t cs) {
 cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                  uint8_t *const *out_u8, float *out_f32, int f32_plane,
-                                 const uint32_t *tiles, int *counters, int *err, cudaStream_t cs) {
+                                 const uint32_t *tiles, int *counters, int *err, cudaStream_t cs,
+                                 bool chroma_pairs) {
+    if (chroma_pairs && (g.planes != 3 || out_u8[2] != out_u8[1] + 4 || ((uintptr_t)out_u8[1] & 15)))
+        return cudaErrorInvalidValue;
     TileArgs a;
     memset(&a, 0, sizeof(a));
     a.g = g;
@@ -810,6 +815,7 @@ cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const in
     }
     a.out_f32 = out_f32;
     a.f32_plane = f32_plane;
+    a.out_pair = chroma_pairs ? 1 : 0;
     a.tiles = tiles;
     a.count = counters;
     a.work = counters + 2;

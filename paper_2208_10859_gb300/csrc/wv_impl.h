@@ -136,6 +136,10 @@ struct TileArgs {
     // opened): a table entry at or above it reads as an absent block and
     // records WV_ERR_FORMAT
     int n_slots;
+    // strip kernel: chroma (planes 1, 2) in groups of 4 samples, Cb and Cr
+    // groups alternating (8 bytes per 4 positions), out_u8[2] = out_u8[1] + 4;
+    // the resampler loads both planes' taps with one 8-byte load
+    int out_pair;
     int a_floats, p_floats;
     // 9/7: half the dequantisation step times the synthesis band scaling
     // folded over all levels.  Synthesis scales a low band by K and a high
@@ -161,6 +165,7 @@ struct ResampleArgs {
     // viewport (out_w x out_h, tightly packed), for the post-filter
     float *y_plane;
     uint8_t *cb_plane, *cr_plane;
+    int c_pair;   // plane[1] holds Cb and Cr in alternating 4-sample groups (plane[2] unused)
 };
 
 // ---- batched decoding ---------------------------------------------------------
@@ -228,6 +233,9 @@ cudaError_t paper_transcode(const void *bytes, size_t n, const PaperInfo &info, 
 int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, int out_w, int out_h,
                   int eye = 0);
 int build_geom(const wv_stream_desc &d, Geom *g, int tile = kTile, int ctile = kCoarseTile);
+// Square-tile organisation with tw x th output tiles (multiples of the mask
+// cell; the batch decoder's shapes).
+int build_geom_rect(const wv_stream_desc &d, Geom *g, int tw, int th, int ctile);
 // Strip geometry (output tiles kStripW x th, th a multiple of 32 in [32, 256])
 // for streams the strip kernel decodes (strip_eligible), else WV_ERR_ARG.
 int build_geom_strip(const wv_stream_desc &d, Geom *g, int th = kStripH, int ctile = kCoarseTile);
@@ -259,14 +267,15 @@ cudaError_t launch_decode_coarse(const Geom &g, const int16_t *payload, const in
 cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                  uint8_t *const *out_u8, float *out_f32, int f32_plane,
-                                 const uint32_t *tiles, int *counters, int *err, cudaStream_t cs);
+                                 const uint32_t *tiles, int *counters, int *err, cudaStream_t cs,
+                                 bool chroma_pairs = false);
 cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
                                const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                uint8_t *const *out_u8, float *out_f32, int f32_plane,
                                const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane = nullptr,
-                     uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr);
+                     uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr, bool c_pair = false);
 void fill_tile_scales(TileArgs &a);
 void smem_needs_cached(int wavelet, int l_top, int l_bot, int tw, int th, int *a_floats, int *p_floats);
 
@@ -286,6 +295,8 @@ cudaError_t launch_decode_batch(int wavelet, int nb, bool fovea, bool dz_t, cons
 // Polls of a batch's bounded device wait before it gives up (the default and
 // the largest a batch accepts; wv_batch_set_wait_limit lowers it)
 constexpr int kBatchWaitPolls = 1 << 21;
+// Default device bytes of one wave of a batch's decode targets.
+constexpr size_t kBatchWaveBytes = size_t(1) << 30;
 // Device allocations of the library (stream stores, batch arenas): cudaMalloc,
 // unless a failure was injected with wv_debug_fail_device_allocs.
 cudaError_t dev_alloc(void **p, size_t bytes);
@@ -293,6 +304,10 @@ cudaError_t dev_alloc(void **p, size_t bytes);
 // least `bytes` (never lowers it); one lock covers the check and the set, so
 // concurrent launches from several host threads cannot undo each other.
 cudaError_t opt_in_smem(const void *fn, int bytes);
+// Whether a stream's reconstruction planes hold chroma as alternating Cb
+// and Cr groups of 4 samples: the strip fine pass writes them so (decode
+// mode 0), the square-tile passes plane by plane.
+bool recon_pairs(const wv_stream *s);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);
@@ -330,6 +345,7 @@ struct wv_stream {
     int ll2_pitch[3] = {0, 0, 0};
     int decode_mode = 0;   // 0: default (strip fine pass), 1: all levels fused per square tile,
                            // 2: coarse pass + square-tile fine pass
+    bool pair_ok = false;  // recon[1], recon[2] adjacent: chroma can be held in alternating groups
     int *counters = nullptr;
     int *err = nullptr;
     // A second set of per-viewport buffers (tile lists, counters, LL_2

@@ -53,7 +53,8 @@ class Request(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_int), ("surfaces", ctypes.c_int), ("coarse_tiles", ctypes.c_int),
-                ("fine_tiles", ctypes.c_int), ("bytes", ctypes.c_size_t), ("ms", ctypes.c_double * 4)]
+                ("fine_tiles", ctypes.c_int), ("bytes", ctypes.c_size_t), ("ms", ctypes.c_double * 4),
+                ("waves", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -162,9 +163,11 @@ def _lib():
             "wv_batch_set_sharing": (c_int, [vp, c_int]),
             "wv_batch_set_wait_limit": (c_int, [vp, c_int]),
             "wv_debug_fail_device_allocs": (None, [c_int]),
-            "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int]),
+            "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
             "wv_batch_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
-                                            ctypes.POINTER(c_int)]),
+                                            ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+            "wv_batch_completion_ms": (c_int, [vp, ctypes.POINTER(ctypes.c_double), c_int]),
+            "wv_batch_set_memory_limit": (c_int, [vp, c_size]),
             "wv_batch_autotune": (c_int, [vp, ctypes.POINTER(Request), c_int, c_int]),
         }
         for name, (res, args) in sig.items():
@@ -197,7 +200,8 @@ def exported_symbols() -> list[str]:
             "wv_batch_create", "wv_batch_close", "wv_batch_decode", "wv_batch_set_cuda_stream",
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
             "wv_batch_set_sharing", "wv_batch_set_wait_limit", "wv_debug_fail_device_allocs",
-            "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune"]
+            "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune", "wv_batch_completion_ms",
+            "wv_batch_set_memory_limit"]
 
 
 def _check(rc: int, what: str):
@@ -423,8 +427,20 @@ class Batch:
         info = BatchInfo()
         _check(_lib().wv_batch_stats(self._h, ctypes.byref(info)), "wv_batch_stats")
         return {"requests": info.requests, "surfaces": info.surfaces, "coarse_tiles": info.coarse_tiles,
-                "fine_tiles": info.fine_tiles, "bytes": info.bytes,
+                "fine_tiles": info.fine_tiles, "bytes": info.bytes, "waves": info.waves,
                 "ms": dict(zip(["footprint", "select", "decode", "resample"], list(info.ms)))}
+
+    def completion_ms(self, n: int) -> np.ndarray:
+        """With timing on: completion time of each request of the last batch
+        (ms from the batch's start; caller order)."""
+        out = np.zeros(n, np.float64)
+        _check(_lib().wv_batch_completion_ms(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n),
+               "wv_batch_completion_ms")
+        return out
+
+    def set_memory_limit(self, nbytes: int) -> None:
+        """Device bytes of decode targets per wave (0: one wave)."""
+        _check(_lib().wv_batch_set_memory_limit(self._h, int(nbytes)), "wv_batch_set_memory_limit")
 
     def set_timing(self, on: bool) -> None:
         _check(_lib().wv_batch_set_timing(self._h, 1 if on else 0), "wv_batch_set_timing")
@@ -436,15 +452,16 @@ class Batch:
         """Polls of the tile decode's bounded wait before it gives up."""
         _check(_lib().wv_batch_set_wait_limit(self._h, int(polls)), "wv_batch_set_wait_limit")
 
-    def set_tile_shape(self, wavelet, levels, width, height, tile, ctile) -> None:
-        _check(_lib().wv_batch_set_tile_shape(self._h, wavelet, levels, width, height, tile, ctile),
+    def set_tile_shape(self, wavelet, levels, width, height, tile_w, tile_h, ctile) -> None:
+        _check(_lib().wv_batch_set_tile_shape(self._h, wavelet, levels, width, height, tile_w, tile_h, ctile),
                "wv_batch_set_tile_shape")
 
     def tile_shape(self, wavelet, levels, width, height) -> tuple:
-        t, c = ctypes.c_int(), ctypes.c_int()
-        _check(_lib().wv_batch_tile_shape(self._h, wavelet, levels, width, height, ctypes.byref(t),
-                                          ctypes.byref(c)), "wv_batch_tile_shape")
-        return t.value, c.value
+        """(output tile width, output tile height, coarse tile side)."""
+        tw, th, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().wv_batch_tile_shape(self._h, wavelet, levels, width, height, ctypes.byref(tw),
+                                          ctypes.byref(th), ctypes.byref(c)), "wv_batch_tile_shape")
+        return tw.value, th.value, c.value
 
     def autotune(self, requests: list, reps: int = 3) -> None:
         _check(_lib().wv_batch_autotune(self._h, _requests(requests), len(requests), reps), "wv_batch_autotune")

@@ -93,7 +93,8 @@ def test_graph_relaunch_takes_new_poses():
     assert b.sync_status() == 0
 
 
-@pytest.mark.parametrize("shape", [(64, 32), (64, 64), (128, 32)])
+@pytest.mark.parametrize("shape", [(64, 64, 32), (64, 64, 64), (128, 128, 32), (256, 64, 64), (256, 128, 64),
+                                   (256, 128, 32)])
 def test_tile_shapes_give_identical_results(shape):
     from paper_2208_10859_gb300 import wv
     st = _streams("yuv97", "yuv53", "ragged97", "gray97_L6")
@@ -118,12 +119,73 @@ def test_autotune_then_decode():
     b.autotune(reqs, reps=2)
     for name in st:
         p = H.case(name)[1]
-        assert b.tile_shape(p.wavelet, p.levels, p.width, p.height) in [(128, 64), (128, 32), (64, 64), (64, 32)]
+        assert b.tile_shape(p.wavelet, p.levels, p.width, p.height) in [
+            (128, 128, 64), (128, 128, 32), (64, 64, 64), (64, 64, 32), (256, 64, 64), (256, 128, 64)]
     b.decode(reqs)
     torch.cuda.synchronize()
     for r in reqs:
         _assert_same(r, r.out.cpu().numpy())
     assert b.sync_status() == 0
+
+
+def test_unsupported_tile_shapes_are_rejected():
+    from paper_2208_10859_gb300 import wv
+    b = wv.Batch()
+    for shape in [(256, 256, 64), (128, 64, 64), (96, 96, 64), (128, 128, 48)]:
+        with pytest.raises(wv.WVError):
+            b.set_tile_shape(1, 5, 8192, 8192, *shape)
+    b.close()
+
+
+@pytest.mark.parametrize("part", [0, 3])
+def test_waves_under_a_memory_limit_change_nothing(part):
+    """Decode targets grouped into waves that reuse one device region: the
+    outputs equal the single decodes; with a limit below any target's size
+    every target is a wave of its own; requests of an earlier wave complete
+    no later than those of a later one."""
+    from paper_2208_10859_gb300 import wv
+    st = _streams(*NAMES)
+    reqs = _requests(st, 14, seed=6)
+    one = wv.Batch()
+    one.set_memory_limit(0)
+    limit = one.device_bytes(reqs) // part if part else 1
+    b = wv.Batch()
+    b.set_memory_limit(limit)
+    b.decode(reqs)
+    torch.cuda.synchronize()
+    assert b.sync_status() == 0
+    info = b.stats()
+    assert info["waves"] > 1
+    if limit == 1:
+        assert info["waves"] == info["surfaces"]
+    for r in reqs:
+        _assert_same(r, r.out.cpu().numpy())
+    one.decode(reqs)
+    torch.cuda.synchronize()
+    i1 = one.stats()
+    assert i1["waves"] == 1
+    assert (i1["fine_tiles"], i1["coarse_tiles"]) == (info["fine_tiles"], info["coarse_tiles"])
+    assert info["bytes"] < i1["bytes"]
+    # completion times follow the waves (timed mode, direct launches)
+    b.set_timing(True)
+    b.decode(reqs)
+    done = b.completion_ms(len(reqs))
+    assert np.all(done > 0)
+    targets = []
+    for r in reqs:
+        k = (id(r.stream), r.frame)
+        if k not in targets:
+            targets.append(k)
+    wave_of = [targets.index((id(r.stream), r.frame)) for r in reqs] if limit == 1 else None
+    if wave_of is not None:
+        order = np.argsort(wave_of, kind="stable")
+        assert np.all(np.diff(done[order]) >= 0)
+    for r in reqs:
+        _assert_same(r, r.out.cpu().numpy())
+    with pytest.raises(wv.WVError):
+        b.completion_ms(len(reqs) + 1)
+    b.close()
+    one.close()
 
 
 def test_timing_mode_and_default_context():

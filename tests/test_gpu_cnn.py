@@ -160,7 +160,11 @@ def test_checkpoint_resume_equals_unbroken_run(tmp_path):
     """Training checkpointed half-way and resumed in a new network object
     (parameters, Adam moments and step count, sampling generator, loss log)
     follows the unbroken run: the same losses at every logged step and the
-    same final parameters."""
+    same final parameters.  The weight gradients are summed over CTAs with
+    float atomics, whose order varies from run to run, so two runs agree to
+    rounding only: the bounds (losses to 1e-4 relative, parameters to 1e-5,
+    1 % of one Adam step at this learning rate) lie far below what a lost
+    moment or a wrong step count changes."""
     from paper_2208_10859_gb300 import wv
     from paper_2208_10859_gb300 import train_postfilter as TP
     rng = np.random.default_rng(12)
@@ -189,8 +193,8 @@ def test_checkpoint_resume_equals_unbroken_run(tmp_path):
     log_a, net_a = run(False)
     log_b, net_b = run(True)
     assert [i for i, _ in log_a] == [i for i, _ in log_b] == list(range(steps))
-    np.testing.assert_allclose([l for _, l in log_b], [l for _, l in log_a], rtol=1e-5, atol=0)
-    np.testing.assert_allclose(net_b.params(), net_a.params(), rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose([l for _, l in log_b], [l for _, l in log_a], rtol=1e-4, atol=0)
+    np.testing.assert_allclose(net_b.params(), net_a.params(), rtol=0, atol=1e-5)
     assert net_a.state()[2] == net_b.state()[2] == steps
     assert net_a.sync_status() == 0 and net_b.sync_status() == 0
     net_a.close()
