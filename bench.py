@@ -571,6 +571,11 @@ def postfilter_leg(args, dev, frames8k, s, poses, stream):
         d = (a[..., :3].float() - b[..., :3].float())
         return float(10 * torch.log10(255.0 ** 2 / (d * d).mean()))
 
+    def psnr_y(a, b):   # luma (BT.709 weights of R, G, B), the plane the filter acts on
+        wy = torch.tensor([0.2126, 0.7152, 0.0722], device=a.device)
+        d = ((a[..., :3].float() - b[..., :3].float()) * wy).sum(-1)
+        return float(10 * torch.log10(255.0 ** 2 / (d * d).mean()))
+
     flops = 2.0 * OUT * OUT * sum(9 * ci * co for co, ci in wv.CNN_SHAPES)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for q in FILTER_STEPS:
@@ -584,6 +589,8 @@ def postfilter_leg(args, dev, frames8k, s, poses, stream):
         torch.cuda.synchronize()
         p_plain = float(np.mean([psnr(a, r) for a, r in zip(plain, ref)]))
         p_filt = float(np.mean([psnr(a, r) for a, r in zip(filt, ref)]))
+        y_plain = float(np.mean([psnr_y(a, r) for a, r in zip(plain, ref)]))
+        y_filt = float(np.mean([psnr_y(a, r) for a, r in zip(filt, ref)]))
         times = {}
         for name, fn in (("plain", st.decode_viewport), ("filtered", None)):
             e0.record(stream)
@@ -607,6 +614,7 @@ def postfilter_leg(args, dev, frames8k, s, poses, stream):
         if net.sync_status() != 0:
             raise RuntimeError("device error in the post-filter")
         res[f"step {q:g}"] = {"psnr_plain_db": p_plain, "psnr_filtered_db": p_filt, "gain_db": p_filt - p_plain,
+                               "luma_psnr_plain_db": y_plain, "luma_gain_db": y_filt - y_plain,
                                "ms_per_viewport": times, "viewports_per_s_filtered": 1e3 / times["filtered"],
                                "network_ms": cnn_ms, "network_tflops": flops / (cnn_ms / 1e3) / 1e12,
                                "weights": os.path.basename(nearest_weights(q))}

@@ -1,17 +1,24 @@
 """Train the residual post-filter (wv_cnn_*) on the GPU and write its
 parameters.
 
-Training pairs: seeded synthetic equirectangular luma frames (band-limited
-noise and textured discs, 2048 x 2048), coded with the library's encoder
-(5-level CDF 9/7 at one dead-zone step: 4, 6, 8, 12 or 16) and decoded with
-the library's decoder (which matches the CPU reference codec within 1e-4 of
-the 8-bit scale); 256 x 256 crops of (decoded, original) luma / 255.  One
+Training pairs (--pairs, the shipped weights): a file of (decoded, original)
+viewport luma pairs written by the oracle codec's pair generator
+(oracle/filter_pairs.py): crops of seeded synthetic 8192 x 8192 frames coded
+as YCbCr 4:2:0, 5-level CDF 9/7, one inter-frame Haar level, at one
+dead-zone step, and projected into viewports with the same sampling as the
+benchmark's 2160 x 2160, 110-degree viewports of 8192 frames, i.e. exactly
+what the filtered decode feeds the network.  The last eighth of the
+viewports (another crop) is held out.  Without --pairs: grey 2048 x 2048
+frames coded and decoded by the library itself, whole-plane crops.
+
+256 x 256 crops of (decoded, original) luma / 255 are the samples.  One
 parameter set per step (the artefacts differ in strength; a single set
 smooths low-distortion frames too much).  The network is trained with the
-library's own forward/backward kernels (MSE, Adam).  A held-out set of
-frames gives the PSNR before and after.
+library's own forward/backward kernels (MSE, Adam).  The held-out set gives
+the PSNR before and after.
 
-    python -m paper_2208_10859_gb300.train_postfilter --step 4
+    python -m oracle.filter_pairs --out /tmp/pairs --step 4
+    python -m paper_2208_10859_gb300.train_postfilter --step 4 --pairs /tmp/pairs/pairs_q4.npz
 """
 from __future__ import annotations
 
@@ -136,6 +143,7 @@ def main():
     ap.add_argument("--checkpoint", default=None, help="checkpoint file (written every --every iterations)")
     ap.add_argument("--every", type=int, default=500)
     ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
+    ap.add_argument("--pairs", default=None, help="npz of (decoded, original) viewport luma pairs (dec, org)")
     args = ap.parse_args()
     import torch
     sys.path.insert(0, ROOT)
@@ -144,8 +152,15 @@ def main():
     __graft_entry__.build()
     t0 = time.time()
     out = args.out or weights_path(args.step)
-    dec, org = coded_pairs(wv, torch, (101, 102, 103, 104, 105, 106), (args.step,))
-    tdec, torg = coded_pairs(wv, torch, (201,), (args.step,), frames_per_seed=4)
+    if args.pairs:
+        z = np.load(args.pairs)
+        d = torch.from_numpy(z["dec"]).cuda().float() / 255
+        o = torch.from_numpy(z["org"]).cuda().float() / 255
+        hold = max(1, d.shape[0] // 8)
+        dec, org, tdec, torg = d[:-hold], o[:-hold], d[-hold:], o[-hold:]
+    else:
+        dec, org = coded_pairs(wv, torch, (101, 102, 103, 104, 105, 106), (args.step,))
+        tdec, torg = coded_pairs(wv, torch, (201,), (args.step,), frames_per_seed=4)
     g = torch.Generator(device="cpu").manual_seed(args.seed)
     net = wv.CNN(seed=args.seed)
     steps = int(args.epochs * args.patches / args.batch)
@@ -168,7 +183,9 @@ def main():
     p = net.params()
     os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
     p.astype("<f4").tofile(out)
-    meta = {"patches": args.patches, "patch": PATCH, "batch": args.batch, "steps": steps, "lr": args.lr,
+    meta = {"pairs": os.path.basename(args.pairs) if args.pairs else "library codec, grey 2048^2 frames",
+            "train_images": int(dec.shape[0]), "held_out_images": int(tdec.shape[0]),
+            "patches": args.patches, "patch": PATCH, "batch": args.batch, "steps": steps, "lr": args.lr,
             "train_seconds": train_s, "total_seconds": time.time() - t0, "loss_log": log,
             "held_out_psnr": res, "params": int(p.size)}
     with open(os.path.splitext(out)[0] + ".json", "w") as f:
