@@ -892,6 +892,14 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
     if (!s || frame < 0 || frame >= s->g.num_frames || plane < 0 || plane >= s->g.planes)
         return WV_ERR_ARG;
     if (!dptr && as_float) return WV_ERR_ARG;
+    // the strip fine pass writes 8-bit samples only: float output runs the
+    // square-tile passes (the same arithmetic per sample)
+    struct ModeGuard {
+        wv_stream *s;
+        int saved;
+        ~ModeGuard() { s->decode_mode = saved; }
+    } guard{s, s->decode_mode};
+    if (as_float && strip_mode(s)) s->decode_mode = 2;
     const Geom &g = active_geom(s);
     uint8_t *outs[3] = {s->recon[0], s->recon[1], s->recon[2]};
     float *f32 = nullptr;

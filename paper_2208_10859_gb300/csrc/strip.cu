@@ -530,7 +530,6 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
     const float *llp = a.ll_in[plane];
     const int llpitch = a.ll_in_pitch[plane];
     const bool writer = lane >= 1 && lane <= 28 && (!EDGE || l1.c0 + 8 <= W);
-    const bool to_f32 = a.out_f32 && plane == a.f32_plane;
     uint8_t *out8 = a.out_u8[plane];
     const int pair_sh = a.out_pair && plane > 0 ? 1 : 0;
 
@@ -707,25 +706,17 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                     for (int rr2 = 0; rr2 < 2; ++rr2) {
                         const T *v = rr2 ? oo : oe;
                         const size_t o = (size_t)(r0 + rr2) * W + l1.c0;
-                        if (to_f32) {
-                            float f[8];
+                        int p[8];
 #pragma unroll
-                            for (int m = 0; m < 8; ++m) f[m] = (float)v[m] + 128.0f;
-                            *reinterpret_cast<float4 *>(a.out_f32 + o) = make_float4(f[0], f[1], f[2], f[3]);
-                            *reinterpret_cast<float4 *>(a.out_f32 + o + 4) = make_float4(f[4], f[5], f[6], f[7]);
-                        } else {
-                            int p[8];
-#pragma unroll
-                            for (int m = 0; m < 8; ++m) {
-                                if constexpr (WAV == 1) p[m] = __float2int_rd(v[m] + 128.5f);
-                                else p[m] = v[m] + 128;
-                            }
-                            // two groups of 4 samples: adjacent, or (chroma groups)
-                            // with the other chroma plane's group between them
-                            uint32_t *d = reinterpret_cast<uint32_t *>(out8 + (o << pair_sh));
-                            d[0] = pack4_sat(p[0], p[1], p[2], p[3]);
-                            d[1 << pair_sh] = pack4_sat(p[4], p[5], p[6], p[7]);
+                        for (int m = 0; m < 8; ++m) {
+                            if constexpr (WAV == 1) p[m] = __float2int_rd(v[m] + 128.5f);
+                            else p[m] = v[m] + 128;
                         }
+                        // two groups of 4 samples: adjacent, or (chroma groups)
+                        // with the other chroma plane's group between them
+                        uint32_t *d = reinterpret_cast<uint32_t *>(out8 + (o << pair_sh));
+                        d[0] = pack4_sat(p[0], p[1], p[2], p[3]);
+                        d[1 << pair_sh] = pack4_sat(p[4], p[5], p[6], p[7]);
                     }
                 }
             }
@@ -813,8 +804,10 @@ cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const in
         a.ll_in_pitch[p] = ll2 ? ll2_pitch[p] : 0;
         a.out_u8[p] = out_u8[p];
     }
-    a.out_f32 = out_f32;
-    a.f32_plane = f32_plane;
+    // 8-bit samples only (float output takes the square-tile pass): the
+    // float store path cost the kernel 16 spilled bytes and 9 % of its time
+    if (out_f32) return cudaErrorInvalidValue;
+    (void)f32_plane;
     a.out_pair = chroma_pairs ? 1 : 0;
     a.tiles = tiles;
     a.count = counters;
