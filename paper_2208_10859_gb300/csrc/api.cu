@@ -198,7 +198,7 @@ int check_image(const wv_image *o) {
 // planes) followed by a fine pass (levels 2 and 1), or all levels in one
 // pass when the stream has fewer than three levels or mode 1 is set.
 // The fine pass (levels 2 and 1) of the listed tiles: strips, or square tiles
-// reading LL_2 from the planes.  ll2 == null: two-level streams (strips only).
+// reading LL_2 from the planes.
 cudaError_t launch_fine(wv_stream *s, const Bands &b, const float *const *ll2, uint8_t *const *out_u8,
                         float *f32, int f32_plane, const uint32_t *tiles, int *counters,
                         cudaStream_t cs) {
@@ -231,11 +231,8 @@ cudaError_t run_decode(wv_stream *s, const Bands &b, uint8_t *const *out_u8, flo
         return e;
     }
     prof_begin(s, kKFine);
-    if (strip_mode(s))   // two levels: LL_2 is the stream's LL band
-        e = launch_fine(s, b, nullptr, out_u8, f32, f32_plane, s->tiles, s->counters, s->cs);
-    else
-        e = launch_decode_tiles(g, s->payload, s->table, b, out_u8, f32, f32_plane, s->tiles,
-                                s->counters, s->err, s->cs);
+    e = launch_decode_tiles(g, s->payload, s->table, b, out_u8, f32, f32_plane, s->tiles, s->counters, s->err,
+                            s->cs);
     prof_end(s);
     return e;
 }
@@ -595,11 +592,12 @@ int build_geom_rect(const wv_stream_desc &d, Geom *g, int tw, int th, int ctile)
     return build_geom_tiles(d, g, tw, th, 0, ctile);
 }
 
-// The strip kernel decodes levels 2 and 1 of dead-zone streams (LL_2 from the
-// coarse pass, or the LL band itself at two levels) and addresses the payload
-// with 32-bit element offsets.
+// The strip kernel decodes levels 2 and 1 of dead-zone streams of three or
+// more levels (LL_2 from the coarse pass; taking it from the LL band of
+// two-level streams in the same loop cost 5 % in spilled registers) and
+// addresses the payload with 32-bit element offsets.
 bool strip_eligible(const wv_stream_desc &d, uint64_t n_payload) {
-    return d.levels >= 2 && d.quant == 0 &&
+    return d.levels >= 3 && d.quant == 0 &&
            n_payload * (uint64_t)d.block * (uint64_t)d.block < (1ull << 32);
 }
 

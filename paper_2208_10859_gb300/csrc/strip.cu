@@ -526,7 +526,6 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
     l2.scalar = EDGE && !wide && !l2.fast && !l2.zero;
     const bool right = X0 > 0;   // an edge strip of a wide plane: its right side, else its left
     const int C2 = (X0 >> 1) - 8;            // LL_1 column of ring column 0
-    const bool ll_plane = a.ll_in[plane] != nullptr;   // LL_2 from the coarse pass, else the LL band
     const float *llp = a.ll_in[plane];
     const int llpitch = a.ll_in_pitch[plane];
     const bool writer = lane >= 1 && lane <= 28 && (!EDGE || l1.c0 + 8 <= W);
@@ -554,11 +553,7 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
         if (t < P2) {
             const int sig = (Y0 >> 1) - 6 + 2 * t;
             const int ke = refl(sig, H2) >> 1, ko = refl(sig + 1, H2) >> 1;
-            if (ll_plane) {
-                cp_async(St::ll(sb, lane), l2.fast ? llp + (size_t)ke * llpitch + l2.kx : llp, 8, l2.fast);
-            } else {
-                sub_issue<NB, 1>(a, pg, 2, 0, ke, l2, r2[0], [&](int b) { return St::l2(sb, 0, b, lane); });
-            }
+            cp_async(St::ll(sb, lane), l2.fast ? llp + (size_t)ke * llpitch + l2.kx : llp, 8, l2.fast);
             sub_issue<NB, 1>(a, pg, 2, 1, ke, l2, r2[1], [&](int b) { return St::l2(sb, 1, b, lane); });
             sub_issue<NB, 1>(a, pg, 2, 2, ko, l2, r2[2], [&](int b) { return St::l2(sb, 2, b, lane); });
             sub_issue<NB, 1>(a, pg, 2, 3, ko, l2, r2[3], [&](int b) { return St::l2(sb, 3, b, lane); });
@@ -594,19 +589,14 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
             {
                 T ll[2], hl[2], lh[2], hh[2];
                 uint32_t w[NB][1];
-                if (ll_plane) {
-                    if (!l2.scalar) {
-                        const float2 x = *reinterpret_cast<const float2 *>(St::ll(sb, lane));
-                        ll[0] = from_f<T>(x.x);
-                        ll[1] = from_f<T>(x.y);
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < 2; ++m)
-                            ll[m] = from_f<T>(__ldcg(llp + (size_t)ke * llpitch + (refl(l2.c0 + 2 * m, W2) >> 1)));
-                    }
+                if (!l2.scalar) {
+                    const float2 x = *reinterpret_cast<const float2 *>(St::ll(sb, lane));
+                    ll[0] = from_f<T>(x.x);
+                    ll[1] = from_f<T>(x.y);
                 } else {
-                    sub_fetch<NB, 1>(a, pg, 2, 0, 0, W2, ke, l2, [&](int b) { return St::l2(sb, 0, b, lane); }, w);
-                    dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][0], ll);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+                        ll[m] = from_f<T>(__ldcg(llp + (size_t)ke * llpitch + (refl(l2.c0 + 2 * m, W2) >> 1)));
                 }
                 sub_fetch<NB, 1>(a, pg, 2, 1, 1, W2, ke, l2, [&](int b) { return St::l2(sb, 1, b, lane); }, w);
                 dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][1], hl);
@@ -779,8 +769,8 @@ cudaError_t launch_nb(const TileArgs &a, cudaStream_t cs) {
 
 }  // namespace
 
-// Levels 2 and 1 of the listed strip tiles: LL_2 from the planes written by
-// the coarse pass (ll2 != null) or, for two-level streams, from the LL band.
+// Levels 2 and 1 of the listed strip tiles, LL_2 from the planes written by
+// the coarse pass (streams of three or more levels).
 cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const int32_t *table,
                                  const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                  uint8_t *const *out_u8, float *out_f32, int f32_plane,
@@ -813,7 +803,7 @@ cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const in
     a.count = counters;
     a.work = counters + 2;
     fill_tile_scales(a);
-    if (!g.strip || g.levels < 2 || g.quant != 0) return cudaErrorInvalidValue;
+    if (!g.strip || g.levels < 3 || g.quant != 0 || !ll2) return cudaErrorInvalidValue;
     if (g.wavelet == WV_WAVELET_97) return g.dz_t ? launch_nb<1, 2>(a, cs) : launch_nb<1, 0>(a, cs);
     return launch_nb<0, 0>(a, cs);
 }
