@@ -109,6 +109,15 @@ def test_coarse_fine_split_equals_fused(name):
                 np.testing.assert_array_equal(a, b)
             else:
                 assert np.abs(a.astype(np.float64) - b).max() <= H.tol_97_levels()
+            # 8-bit samples: the strip fine pass (mode 0; float output always
+            # takes the square tiles) equals the square-tile fine pass
+            # (mode 2) exactly -- the same lifting arithmetic per sample
+            s.set_decode_mode(0)
+            u_strip = _decode(s, f, pl, False)
+            s.set_decode_mode(2)
+            u_square = _decode(s, f, pl, False)
+            np.testing.assert_array_equal(u_strip, u_square)
+    s.set_decode_mode(1)
     assert s.launches_per_viewport() == 4
     s.set_decode_mode(0)
     assert s.launches_per_viewport() == (5 if p.levels >= 3 else 4)
