@@ -119,6 +119,8 @@ struct Layout {
 Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
     Geom g = g0;
     g.total_tiles = std::max(g0.total_tiles, gsq.total_tiles);
+    // tile lists: an edge strip is listed as two half strips
+    const size_t list_tiles = std::max<size_t>(2 * (size_t)g0.total_tiles, gsq.total_tiles);
     Layout L;
     size_t o = 0;
     L.payload = o;
@@ -137,7 +139,7 @@ Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
     L.mask = o;
     o = align256(o + (size_t)g.cells_x * g.cells_y);
     L.tiles = o;
-    o = align256(o + (size_t)g.total_tiles * 4);
+    o = align256(o + list_tiles * 4);
     L.ctiles = o;
     o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
     L.tile_gen = o;
@@ -154,7 +156,7 @@ Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
             o = align256(o + (size_t)g.p[p].ll2_pitch * (g.p[p].h >> 2) * 4);
     }
     L.tiles1 = o;
-    o = align256(o + (size_t)g.total_tiles * 4);
+    o = align256(o + list_tiles * 4);
     L.ctiles1 = o;
     o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
     L.counters1 = o;

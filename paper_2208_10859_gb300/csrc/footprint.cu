@@ -206,9 +206,16 @@ __global__ void k_select_tiles(Geom g, const uint32_t *__restrict__ tile_gen,
     const int t0 = coarse ? tid - g.total_tiles : tid;
     const bool valid = coarse ? t0 < g.total_ctiles : true;
     bool sel = valid && (coarse ? ctile_gen[t0] : tile_gen[t0]) == gen;
-    const uint32_t entry = sel ? tile_entry(g, t0, coarse) : 0u;
-    // warps straddling the two ranges: both calls are made by all lanes
+    uint32_t entry = sel ? tile_entry(g, t0, coarse) : 0u;
+    // edge strips are listed as two half strips (their reflected columns
+    // make them the slowest tiles; halves halve their latency)
+    const bool split = sel && !coarse && g.strip &&
+                       !strip_interior((int)(entry & 0x3fff), g.p[(entry >> 28) & 3].w) &&
+                       (int)((entry >> 14) & 0x3fff) * g.th + g.th / 2 < g.p[(entry >> 28) & 3].h;
+    if (split) entry |= kHalfStrip;
+    // warps straddling the two ranges: every call is made by all lanes
     append(sel && !coarse, entry, tiles, &counters[0]);
+    append(split, entry | kLowerHalf, tiles, &counters[0]);
     append(sel && coarse, entry, ctiles, &counters[1]);
 }
 

@@ -501,13 +501,15 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
     using St = Stage<NB>;
     constexpr int D = SV<WAV>::D, P0 = SV<WAV>::P0;
     const Geom &g = a.g;
-    const int plane = (int)(e >> 28);
+    const int plane = (int)((e >> 28) & 3);
     const int ty = (int)((e >> 14) & 0x3fff), tx = (int)(e & 0x3fff);
     const PlaneGeom &pg = g.p[plane];
     const int W = pg.w, H = pg.h;            // level-1 interleaved line lengths
     const int W2 = W >> 1, H2 = H >> 1;      // level-2 interleaved line lengths (LL_1 size)
-    const int X0 = tx * kStripW, Y0 = ty * a.th;
-    const int TH = min(a.th, H - Y0);
+    const int th = (e & kHalfStrip) ? a.th >> 1 : a.th;
+    const int X0 = tx * kStripW, Y0 = ty * a.th + ((e & kLowerHalf) ? th : 0);
+    const int TH = min(th, H - Y0);
+    if (TH <= 0) return;
     // edge strips of planes at least 256 wide touch one side only and find
     // every mirror image in an interior lane of the warp
     const bool wide = W >= 256;
@@ -729,10 +731,10 @@ __global__ void __launch_bounds__(32 * kStripWarps, 3) k_strip(TileArgs a) {
     // SM gets the same share of busy warps
     for (int t = blockIdx.x + wi * gridDim.x; t < count; t += kStripWarps * gridDim.x) {
         const uint32_t e = a.tiles[t];
-        const int tx = (int)(e & 0x3fff), w = a.g.p[e >> 28].w;
-        // interior strips: level-1 and level-2 lanes 0..31 all inside the plane
-        if (tx > 0 && tx * kStripW + 248 <= w) strip_tile<WAV, NB, QM, false>(a, e, ring, stage, lane);
-        else strip_tile<WAV, NB, QM, true>(a, e, ring, stage, lane);
+        if (strip_interior((int)(e & 0x3fff), a.g.p[(e >> 28) & 3].w))
+            strip_tile<WAV, NB, QM, false>(a, e, ring, stage, lane);
+        else
+            strip_tile<WAV, NB, QM, true>(a, e, ring, stage, lane);
     }
 }
 

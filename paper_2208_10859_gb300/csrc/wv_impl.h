@@ -37,6 +37,13 @@ constexpr int kStripW = 224;    // output columns of a strip tile (one warp: 28 
 #define WV_STRIP_H 64
 #endif
 constexpr int kStripH = WV_STRIP_H;   // default output rows of a strip tile
+// Strip tile entries (plane << 28 | ty << 14 | tx) with kHalfStrip set stand
+// for half a strip (rows th/2), the lower half when kLowerHalf is set too:
+// the tile selection splits the edge strips so, whose reflected columns
+// make them the slowest.
+constexpr uint32_t kHalfStrip = 1u << 31, kLowerHalf = 1u << 30;
+// Interior strip: every level-1 and level-2 lane inside a plane of width w.
+__host__ __device__ __forceinline__ bool strip_interior(int tx, int w) { return tx > 0 && tx * kStripW + 248 <= w; }
 
 // Subband index inside a level: 0 = LL (level L only), 1 = HL, 2 = LH, 3 = HH.
 struct PlaneGeom {
