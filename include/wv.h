@@ -490,8 +490,9 @@ int wv_decode_viewport_filtered(wv_stream *s, int frame, float yaw, float pitch,
  * for the lossless workload and for parity checks.  dptr receives width x
  * height samples of the plane, row-major and tightly packed: uint8
  * (as_float = 0) or float32 values before rounding (as_float = 1, 8-bit
- * units, DC offset included).  dptr == NULL decodes into the stream's own
- * reconstruction plane (as uint8) for wv_resample_at. */
+ * units, DC offset included; always the square-tile passes).  dptr == NULL
+ * decodes into the stream's own reconstruction plane (as uint8, in the
+ * layout of the current decode mode) for wv_resample_at. */
 int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float);
 
 /* Decode one whole plane without allocating any device memory.  The paper
@@ -586,7 +587,8 @@ int wv_request_bytes(const wv_request *r, unsigned long long *cone, unsigned lon
 typedef struct {
     double ms[8];        /* footprint, select tiles, coarse decode, fine decode, resample */
     int launches[8];
-    int tiles;           /* tiles decoded by the last viewport */
+    int tiles;           /* tiles decoded by the last viewport (an edge strip
+                            counts as its two halves) */
 } wv_profile;
 
 /* Start recording: the following decode calls on s record events around
@@ -602,13 +604,17 @@ int wv_launches_per_viewport(const wv_stream *s);
 /* Tile-decode organisation.  Mode 0 (default): levels L..3 of the needed
  * coarse tiles go into float LL_2 planes in one kernel (streams of three or
  * more levels), then levels 2 and 1 of the needed output tiles in a second;
- * for dead-zone streams of two or more levels the second kernel streams each
- * 224-column strip of the region down its rows in one warp (strip tiles),
- * otherwise it decodes square 128-sample tiles.  Mode 1: all levels of each
- * square output tile in one kernel, repeating the coarse levels per tile.
- * Mode 2: the coarse pass, then levels 2 and 1 of square output tiles (mode
- * 0 for streams without strip tiles).  Results are identical up to float
- * rounding order for 9/7 and bit-exact for 5/3. */
+ * for dead-zone streams of three or more levels the second kernel streams
+ * each 224-column strip of the region down its rows in one warp (strip
+ * tiles; 8-bit output only: float whole-plane decodes take mode 2), with
+ * the reconstruction's chroma held as alternating Cb and Cr groups of four
+ * samples; otherwise it decodes square 128-sample tiles.  Mode 1: all
+ * levels of each square output tile in one kernel, repeating the coarse
+ * levels per tile.  Mode 2: the coarse pass, then levels 2 and 1 of square
+ * output tiles (mode 0 for streams without strip tiles).  8-bit results are
+ * identical in all modes; float results identical up to float rounding
+ * order for 9/7 and bit-exact for 5/3.  The reconstruction planes follow
+ * the mode: decode again after changing it before wv_resample_at. */
 int wv_set_decode_mode(wv_stream *s, int mode);
 
 /* ---------------------------------------------------------------------------
