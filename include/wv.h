@@ -295,6 +295,13 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info);
  * independent wv_decode_viewport calls, scheduled as one batch). */
 int wv_batch_set_sharing(wv_batch *b, int on);
 
+/* on = 1 (default): decode targets whose streams the strip fine pass takes
+ * (dead-zone codes, three or more levels, one or two coefficient frames)
+ * decode levels 2 and 1 as 224 x 64 strips (k_strip_batch, foveation
+ * included), after the class's coarse tiles; on = 0: square tiles for
+ * every target.  Outputs are identical either way. */
+int wv_batch_set_strips(wv_batch *b, int on);
+
 /* Polls of the tile decode's bounded wait (a fine tile waiting for its
  * target's coarse tiles) before it gives up, records WV_ERR_TIMEOUT in the
  * batch's error word and decodes with what is there (all reads stay in

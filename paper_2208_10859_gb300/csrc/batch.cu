@@ -66,6 +66,7 @@ struct Surface {
     bool foveated;
     Geom g;
     int cls;
+    bool strip;     // fine tiles are strips (k_strip_batch), else square tiles
     int wave;
     size_t bytes;   // device bytes of its stamps, list entries and planes
     size_t recon[3], ll2[3], fmask, stamp;   // arena offsets (inside the wave region)
@@ -81,8 +82,9 @@ struct Wave {
     int s0, s1, r0, r1;
     size_t ctr;            // its counters (kBatchCtr + 2 (s1 - s0) ints)
     size_t stamps, stamp_bytes;
-    size_t lists_c[kClasses], lists_f[kClasses];
+    size_t lists_c[kClasses], lists_f[kClasses], lists_s[kClasses];
     int smem[kClasses];    // dynamic shared memory of each class's decode (0: class absent)
+    bool strip[kClasses];  // the class has strip surfaces in this wave
     int max_cx, max_cy, max_stamps, max_w, max_h;
 };
 
@@ -129,6 +131,7 @@ struct wv_batch {
     bool share = true;                 // unfoveated requests of one (stream, frame) share a surface
     int wait_polls = kBatchWaitPolls;  // polls of the tile decode's bounded wait (arena word at kWaitWord)
     size_t wave_bytes = kBatchWaveBytes;   // device bytes of one wave's surfaces (0: one wave)
+    bool strips = true;                // fine levels of eligible targets as strips
 };
 
 namespace {
@@ -159,7 +162,7 @@ Shape tile_shape(const wv_batch *b, const Geom &g) {
 // reconstruction and LL_2 planes, foveation cell bits (each 256-aligned).
 size_t surface_bytes(const Surface &S) {
     size_t o = sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
-    o += sizeof(uint2) * (S.g.total_tiles + S.g.total_ctiles) + 512;
+    o += sizeof(uint2) * ((S.strip ? 2 : 1) * S.g.total_tiles + S.g.total_ctiles) + 768;
     for (int p = 0; p < S.g.planes; ++p) {
         o += align256((size_t)S.g.p[p].w * S.g.p[p].h);
         if (S.g.levels >= 3) o += align256((size_t)S.g.p[p].ll2_pitch * (S.g.p[p].h >> 2) * 4);
@@ -188,7 +191,13 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         S.foveated = r.fovea != 0;
         const Geom &sg = r.s->g;
         const Shape ts = tile_shape(b, sg);
-        if (build_geom_rect(r.s->desc, &S.g, ts.tw, ts.th, ts.ctile) != WV_OK) return WV_ERR_ARG;
+        // strip tiles for the fine levels where the batched strip pass has
+        // the class (the tuned square shape then only sets the coarse tile)
+        S.strip = b->strips && strip_eligible(r.s->desc, r.s->n_payload) &&
+                  strip_batch_supported(sg.wavelet, 1 + sg.tlevels, sg.dz_t);
+        const int gr = S.strip ? build_geom_strip(r.s->desc, &S.g, kStripH, ts.ctile)
+                               : build_geom_rect(r.s->desc, &S.g, ts.tw, ts.th, ts.ctile);
+        if (gr != WV_OK) return WV_ERR_ARG;
         S.g.dz_t = sg.dz_t;   // the code form of the stream's device payload
         // 1 + tlevels coefficient frames
         const int group = S.g.dz_t ? 4 + (S.foveated ? 1 : 0) : 2 * S.g.wavelet + (S.foveated ? 1 : 0);
@@ -245,13 +254,13 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
     for (Wave &W : P.waves) {
         o = P.region;
         W.stamps = o;
-        size_t tiles[kClasses] = {}, ctiles[kClasses] = {};
+        size_t tiles[kClasses] = {}, ctiles[kClasses] = {}, stiles[kClasses] = {};
         W.max_cx = W.max_cy = W.max_stamps = W.max_w = W.max_h = 0;
         for (int si = W.s0; si < W.s1; ++si) {
             Surface &S = P.surf[si];
             S.stamp = o;
             o += sizeof(uint32_t) * (S.g.total_tiles + S.g.total_ctiles);
-            tiles[S.cls] += S.g.total_tiles;
+            (S.strip ? stiles : tiles)[S.cls] += (S.strip ? 2 : 1) * (size_t)S.g.total_tiles;
             ctiles[S.cls] += S.g.total_ctiles;
             W.max_cx = std::max(W.max_cx, S.g.cells_x);
             W.max_cy = std::max(W.max_cy, S.g.cells_y);
@@ -264,6 +273,9 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
             o = align256(o + sizeof(uint2) * std::max<size_t>(ctiles[c], 1));
             W.lists_f[c] = o;
             o = align256(o + sizeof(uint2) * std::max<size_t>(tiles[c], 1));
+            W.lists_s[c] = o;
+            o = align256(o + sizeof(uint2) * std::max<size_t>(stiles[c], 1));
+            W.strip[c] = stiles[c] > 0;
         }
         for (int si = W.s0; si < W.s1; ++si) {
             Surface &S = P.surf[si];
@@ -341,7 +353,9 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         J.stamp = (uint32_t *)(base + S.stamp);
         J.fmask = S.foveated ? (uint8_t *)(base + S.fmask) : nullptr;
         J.cls = S.cls;
-        int need = (J.fine.a_floats + J.fine.p_floats) * 4;
+        J.strip = S.strip ? 1 : 0;
+        // the class's tile decode takes only the coarse tiles of strip surfaces
+        int need = S.strip ? 0 : (J.fine.a_floats + J.fine.p_floats) * 4;
         if (S.g.levels >= 3) need = std::max(need, (J.coarse.a_floats + J.coarse.p_floats) * 4);
         int &sm = P.waves[S.wave].smem[S.cls];
         sm = std::max(sm, need);
@@ -408,6 +422,7 @@ cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool tim
         for (int c = 0; c < kClasses; ++c) {
             lists.coarse[c] = (uint2 *)(base + W.lists_c[c]);
             lists.fine[c] = (uint2 *)(base + W.lists_f[c]);
+            lists.strip[c] = (uint2 *)(base + W.lists_s[c]);
         }
         launch_select_batch(surfs + W.s0, m, W.max_stamps, lists, ctr, cs);
         if (timed) cudaEventRecord(ev[2], cs);
@@ -418,6 +433,14 @@ cudaError_t enqueue(wv_batch *b, const Plan &P, int n, cudaStream_t cs, bool tim
                                     group >= 4, surfs + W.s0, lists.coarse[c], lists.fine[c], ctr + 4 * c,
                                     ctr + kBatchCtr, (int *)(base + P.err), (const int *)(base + kWaitWord),
                                     W.smem[c], cs);
+            if (e != cudaSuccess) return e;
+        }
+        // the strip tiles, once their class's coarse tiles are done
+        for (int c = 0; c < kClasses; ++c) {
+            if (!W.strip[c]) continue;
+            const int group = c / kMaxBands;
+            e = launch_decode_strips_batch(group >= 4 ? WV_WAVELET_97 : group / 2, c % kMaxBands + 1, group % 2 == 1,
+                                           group >= 4, surfs + W.s0, lists.strip[c], ctr + 4 * c + 3, cs);
             if (e != cudaSuccess) return e;
         }
         if (timed) cudaEventRecord(ev[3], cs);
@@ -440,6 +463,8 @@ std::vector<long long> shape_key(const wv_batch *b, const Plan &P, int n) {
             k.push_back(W.smem[c]);
             k.push_back((long long)W.lists_c[c]);
             k.push_back((long long)W.lists_f[c]);
+            k.push_back((long long)W.lists_s[c]);
+            k.push_back(W.strip[c] ? 1 : 0);
         }
     }
     return k;
@@ -651,7 +676,7 @@ int wv_batch_stats(wv_batch *b, wv_batch_info *info) {
     for (int c0 : b->ctr_base)
         for (int k = 0; k < kClasses; ++k) {
             info->coarse_tiles += c[c0 + 4 * k + 1];
-            info->fine_tiles += c[c0 + 4 * k + 2];
+            info->fine_tiles += c[c0 + 4 * k + 2] + c[c0 + 4 * k + 3];
         }
     info->bytes = b->dbytes;
     if (b->timing) {
@@ -693,6 +718,12 @@ int wv_batch_set_wait_limit(wv_batch *b, int polls) {
 int wv_batch_set_sharing(wv_batch *b, int on) {
     if (!b || on < 0 || on > 1) return WV_ERR_ARG;
     b->share = on != 0;
+    return WV_OK;
+}
+
+int wv_batch_set_strips(wv_batch *b, int on) {
+    if (!b || on < 0 || on > 1) return WV_ERR_ARG;
+    b->strips = on != 0;
     return WV_OK;
 }
 

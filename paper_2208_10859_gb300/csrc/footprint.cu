@@ -245,7 +245,14 @@ __global__ void k_select_batch(const SurfaceJob *__restrict__ surfs, BatchLists 
     uint2 e = make_uint2((uint32_t)si, 0u);
     if (sel) e.y = tile_entry(g, is_coarse ? tid - g.total_tiles : tid, is_coarse);
     const int c = s.cls;
-    append2(sel && !is_coarse, e, lists.fine[c], &ctr[4 * c + 2]);
+    // strip surfaces: fine tiles to the strip list, edge strips as two halves
+    const bool st = sel && !is_coarse && s.strip;
+    const bool split = st && !strip_interior((int)(e.y & 0x3fff), g.p[(e.y >> 28) & 3].w) &&
+                       (int)((e.y >> 14) & 0x3fff) * g.th + g.th / 2 < g.p[(e.y >> 28) & 3].h;
+    if (split) e.y |= kHalfStrip;
+    append2(st, e, lists.strip[c], &ctr[4 * c + 3]);
+    append2(split, make_uint2(e.x, e.y | kLowerHalf), lists.strip[c], &ctr[4 * c + 3]);
+    append2(sel && !is_coarse && !s.strip, e, lists.fine[c], &ctr[4 * c + 2]);
     const unsigned cb = __ballot_sync(0xffffffffu, sel && is_coarse);
     if (cb && (threadIdx.x & 31) == __ffs(cb) - 1) atomicAdd(&ctr[kBatchCtr + 2 * si], __popc(cb));
     append2(sel && is_coarse, e, lists.coarse[c], &ctr[4 * c + 1]);

@@ -186,6 +186,17 @@ __device__ __noinline__ void code1(const TileArgs &a, const PlaneGeom &pg, int l
     }
 }
 
+// Foveated decoding (Sec. 3.7): whether the level-l (l = 1, 2) detail
+// coefficient (kx, ky) of a plane is kept, from the foveation bits of the
+// mask cell holding its nominal luma position (kx 2^l sub, ky 2^l sub).  A
+// lane's coefficients of one subband row (four at level 1, two at level 2)
+// share one cell: strips start on a cell boundary and a lane's columns are
+// 8-aligned.
+__device__ __forceinline__ bool fov_keep(const TileArgs &a, const PlaneGeom &pg, int l, int kx, int ky) {
+    const int X = (kx << l) * pg.sub, Y = (ky << l) * pg.sub;
+    return (__ldg(&a.fmask[(Y >> kLogCell) * a.g.cells_x + (X >> kLogCell)]) >> (l - 1)) & 1;
+}
+
 // ---- asynchronous staging of each lane's coefficient words -----------------
 //
 // Iteration q of a tile reads, per lane, NW words of each level-2 subband
@@ -235,7 +246,7 @@ struct Stage {
 // (zero lanes: zero fill).
 template <int NB, int NW, class Dst>
 __device__ __forceinline__ void sub_issue(const TileArgs &a, const PlaneGeom &pg, int level, int sub, int kr,
-                                          const LaneCols &lc, SubRow<NB> &r, Dst dst) {
+                                          const LaneCols &lc, SubRow<NB> &r, Dst dst, bool keep = true) {
     const Geom &g = a.g;
     // one path for every lane: lanes without a vector load copy zero bytes
     // (zero fill); the block row is the warp's, so the refresh is uniform
@@ -244,14 +255,14 @@ __device__ __forceinline__ void sub_issue(const TileArgs &a, const PlaneGeom &pg
     const uint32_t roff = (uint32_t)(kr & (g.block - 1)) << g.log2b;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const bool have = r.off[b] != kNone;   // kNone for all but vector lanes
+        const bool have = r.off[b] != kNone && keep;   // kNone for all but vector lanes
         cp_async(dst(b), a.payload + (have ? r.off[b] + roff : 0u), 4 * NW, have);
     }
 }
 
 // Codes of a lane whose columns leave the plane, one at a time at the
 // reflected column (out of line: edge strips only).
-template <int NB, int NW>
+template <int NB, int NW, bool FOV>
 __device__ __noinline__ void sub_fetch_slow(const TileArgs &a, const PlaneGeom &pg, int level, int sub, int par,
                                             int n2, int kr, int c0, uint32_t (&w)[NB][NW]) {
 #pragma unroll
@@ -263,6 +274,9 @@ __device__ __noinline__ void sub_fetch_slow(const TileArgs &a, const PlaneGeom &
         const int kc = refl(c0 + 2 * m + par, n2) >> 1;
         uint32_t v[NB];
         code1<NB>(a, pg, level, sub, kc, kr, v);
+        if (FOV && !fov_keep(a, pg, level, kc, kr))
+#pragma unroll
+            for (int b = 0; b < NB; ++b) v[b] = 0u;
 #pragma unroll
         for (int b = 0; b < NB; ++b) w[b][m >> 1] |= v[b] << (16 * (m & 1));
     }
@@ -271,7 +285,7 @@ __device__ __noinline__ void sub_fetch_slow(const TileArgs &a, const PlaneGeom &
 // The lane's NW words of a subband row: from the stage (vector lanes), or
 // one code at a time at the reflected column (interleaved parity `par`, line
 // length `n2` = twice the subband width).
-template <int NB, int NW, class Src>
+template <int NB, int NW, bool FOV = false, class Src>
 __device__ __forceinline__ void sub_fetch(const TileArgs &a, const PlaneGeom &pg, int level, int sub, int par,
                                           int n2, int kr, const LaneCols &lc, Src src, uint32_t (&w)[NB][NW]) {
     if (!lc.scalar) {
@@ -287,7 +301,7 @@ __device__ __forceinline__ void sub_fetch(const TileArgs &a, const PlaneGeom &pg
             }
         }
     } else {
-        sub_fetch_slow<NB, NW>(a, pg, level, sub, par, n2, kr, lc.c0, w);
+        sub_fetch_slow<NB, NW, FOV>(a, pg, level, sub, par, n2, kr, lc.c0, w);
     }
 }
 
@@ -494,7 +508,7 @@ __device__ __forceinline__ uint32_t pack4_sat(int p0, int p1, int p2, int p3) {
 // right side (mirror_row, and codes loaded one at a time for the edge lanes
 // of planes narrower than 256).
 
-template <int WAV, int NB, int QM, bool EDGE>
+template <int WAV, int NB, int QM, bool EDGE, bool FOV = false>
 __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float *ring, uint32_t *stage,
                                            int lane) {
     using T = typename SV<WAV>::T;
@@ -556,18 +570,22 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
             const int sig = (Y0 >> 1) - 6 + 2 * t;
             const int ke = refl(sig, H2) >> 1, ko = refl(sig + 1, H2) >> 1;
             cp_async(St::ll(sb, lane), l2.fast ? llp + (size_t)ke * llpitch + l2.kx : llp, 8, l2.fast);
-            sub_issue<NB, 1>(a, pg, 2, 1, ke, l2, r2[1], [&](int b) { return St::l2(sb, 1, b, lane); });
-            sub_issue<NB, 1>(a, pg, 2, 2, ko, l2, r2[2], [&](int b) { return St::l2(sb, 2, b, lane); });
-            sub_issue<NB, 1>(a, pg, 2, 3, ko, l2, r2[3], [&](int b) { return St::l2(sb, 3, b, lane); });
+            const bool ke2 = !FOV || !l2.fast || fov_keep(a, pg, 2, l2.kx, ke);
+            const bool ko2 = !FOV || !l2.fast || fov_keep(a, pg, 2, l2.kx, ko);
+            sub_issue<NB, 1>(a, pg, 2, 1, ke, l2, r2[1], [&](int b) { return St::l2(sb, 1, b, lane); }, ke2);
+            sub_issue<NB, 1>(a, pg, 2, 2, ko, l2, r2[2], [&](int b) { return St::l2(sb, 2, b, lane); }, ko2);
+            sub_issue<NB, 1>(a, pg, 2, 3, ko, l2, r2[3], [&](int b) { return St::l2(sb, 3, b, lane); }, ko2);
         }
         if (t - 1 >= P0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int k = (Y0 >> 1) - 2 + 2 * (t - 1 - P0) + h;
                 const int ke1 = refl(2 * k, H) >> 1, ko1 = refl(2 * k + 1, H) >> 1;
-                sub_issue<NB, 2>(a, pg, 1, 1, ke1, l1, r1[1], [&](int b) { return St::l1(sb, h, 1, b, lane); });
-                sub_issue<NB, 2>(a, pg, 1, 2, ko1, l1, r1[2], [&](int b) { return St::l1(sb, h, 2, b, lane); });
-                sub_issue<NB, 2>(a, pg, 1, 3, ko1, l1, r1[3], [&](int b) { return St::l1(sb, h, 3, b, lane); });
+                const bool kee = !FOV || !l1.fast || fov_keep(a, pg, 1, l1.kx, ke1);
+                const bool koo = !FOV || !l1.fast || fov_keep(a, pg, 1, l1.kx, ko1);
+                sub_issue<NB, 2>(a, pg, 1, 1, ke1, l1, r1[1], [&](int b) { return St::l1(sb, h, 1, b, lane); }, kee);
+                sub_issue<NB, 2>(a, pg, 1, 2, ko1, l1, r1[2], [&](int b) { return St::l1(sb, h, 2, b, lane); }, koo);
+                sub_issue<NB, 2>(a, pg, 1, 3, ko1, l1, r1[3], [&](int b) { return St::l1(sb, h, 3, b, lane); }, koo);
             }
         }
         cp_commit();
@@ -600,11 +618,11 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                     for (int m = 0; m < 2; ++m)
                         ll[m] = from_f<T>(__ldcg(llp + (size_t)ke * llpitch + (refl(l2.c0 + 2 * m, W2) >> 1)));
                 }
-                sub_fetch<NB, 1>(a, pg, 2, 1, 1, W2, ke, l2, [&](int b) { return St::l2(sb, 1, b, lane); }, w);
+                sub_fetch<NB, 1, FOV>(a, pg, 2, 1, 1, W2, ke, l2, [&](int b) { return St::l2(sb, 1, b, lane); }, w);
                 dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][1], hl);
-                sub_fetch<NB, 1>(a, pg, 2, 2, 0, W2, ko, l2, [&](int b) { return St::l2(sb, 2, b, lane); }, w);
+                sub_fetch<NB, 1, FOV>(a, pg, 2, 2, 0, W2, ko, l2, [&](int b) { return St::l2(sb, 2, b, lane); }, w);
                 dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][2], lh);
-                sub_fetch<NB, 1>(a, pg, 2, 3, 1, W2, ko, l2, [&](int b) { return St::l2(sb, 3, b, lane); }, w);
+                sub_fetch<NB, 1, FOV>(a, pg, 2, 3, 1, W2, ko, l2, [&](int b) { return St::l2(sb, 3, b, lane); }, w);
                 dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][3], hh);
                 ev[0] = ll[0];
                 ev[1] = hl[0];
@@ -670,11 +688,11 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                         for (int m = 0; m < 4; ++m) ll[m] = T(0);
                     }
                     uint32_t w[NB][2];
-                    sub_fetch<NB, 2>(a, pg, 1, 1, 1, W, ke, l1, [&](int b) { return St::l1(sb, h, 1, b, lane); }, w);
+                    sub_fetch<NB, 2, FOV>(a, pg, 1, 1, 1, W, ke, l1, [&](int b) { return St::l1(sb, h, 1, b, lane); }, w);
                     dq_row<WAV, NB, QM, 2>(a, w, a.scale[1][1], hl);
-                    sub_fetch<NB, 2>(a, pg, 1, 2, 0, W, ko, l1, [&](int b) { return St::l1(sb, h, 2, b, lane); }, w);
+                    sub_fetch<NB, 2, FOV>(a, pg, 1, 2, 0, W, ko, l1, [&](int b) { return St::l1(sb, h, 2, b, lane); }, w);
                     dq_row<WAV, NB, QM, 2>(a, w, a.scale[1][2], lh);
-                    sub_fetch<NB, 2>(a, pg, 1, 3, 1, W, ko, l1, [&](int b) { return St::l1(sb, h, 3, b, lane); }, w);
+                    sub_fetch<NB, 2, FOV>(a, pg, 1, 3, 1, W, ko, l1, [&](int b) { return St::l1(sb, h, 3, b, lane); }, w);
                     dq_row<WAV, NB, QM, 2>(a, w, a.scale[1][3], hh);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
@@ -769,7 +787,72 @@ cudaError_t launch_nb(const TileArgs &a, cudaStream_t cs) {
     }
 }
 
+// Batched decoding: the strip tiles of the decode targets ("surfaces") of
+// one decode class in one launch, after their coarse tiles (another launch).
+// List entries are (surface, strip entry); a tile reads its surface's
+// arguments from the job table (read-only, through the cache).
+template <int WAV, int NB, int QM, bool FOV>
+__global__ void __launch_bounds__(32 * kStripWarps, 3)
+    k_strip_batch(const SurfaceJob *__restrict__ surfs, const uint2 *__restrict__ list, const int *count_p) {
+    __shared__ __align__(16) float rings[kStripWarps][kRing * kRingW];
+    extern __shared__ __align__(16) uint32_t stages[];   // kStripWarps x kStages x Stage<NB>::kWords
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    float *ring = rings[wi];
+    uint32_t *stage = stages + (size_t)wi * kStages * Stage<NB>::kWords;
+    for (int i = lane; i < kRing * kRingW; i += 32) ring[i] = 0.f;
+    __syncwarp();
+    const int count = *(volatile const int *)count_p;
+    for (int t = blockIdx.x + wi * gridDim.x; t < count; t += kStripWarps * gridDim.x) {
+        const uint2 it = list[t];
+        const TileArgs &a = surfs[it.x].fine;
+        const uint32_t e = it.y;
+        if (strip_interior((int)(e & 0x3fff), a.g.p[(e >> 28) & 3].w))
+            strip_tile<WAV, NB, QM, false, FOV>(a, e, ring, stage, lane);
+        else
+            strip_tile<WAV, NB, QM, true, FOV>(a, e, ring, stage, lane);
+    }
+}
+
+template <int WAV, int NB, int QM, bool FOV>
+cudaError_t launch_b(const SurfaceJob *surfs, const uint2 *list, const int *count, cudaStream_t cs) {
+    static std::once_flag once[64];
+    static cudaError_t set_err[64];
+    const int smem = kStripWarps * kStages * Stage<NB>::kWords * 4;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [&] {
+        set_err[dev] =
+            cudaFuncSetAttribute(k_strip_batch<WAV, NB, QM, FOV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    if (set_err[dev] != cudaSuccess) return set_err[dev];
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strip_batch<WAV, NB, QM, FOV>,
+                                                                  32 * kStripWarps, smem);
+    if (e != cudaSuccess) return e;
+    k_strip_batch<WAV, NB, QM, FOV><<<sms * std::max(per_sm, 1), 32 * kStripWarps, smem, cs>>>(surfs, list, count);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool strip_batch_supported(int wavelet, int nb, bool dz_t) {
+    return nb >= 1 && nb <= 2 && (wavelet == WV_WAVELET_53 || dz_t);
+}
+
+cudaError_t launch_decode_strips_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
+                                       const uint2 *list, const int *count, cudaStream_t cs) {
+    if (!strip_batch_supported(wavelet, nb, dz_t)) return cudaErrorInvalidValue;
+    if (wavelet == WV_WAVELET_97) {
+        if (nb == 1) return fovea ? launch_b<1, 1, 2, true>(surfs, list, count, cs)
+                                  : launch_b<1, 1, 2, false>(surfs, list, count, cs);
+        return fovea ? launch_b<1, 2, 2, true>(surfs, list, count, cs) : launch_b<1, 2, 2, false>(surfs, list, count, cs);
+    }
+    if (nb == 1) return fovea ? launch_b<0, 1, 0, true>(surfs, list, count, cs)
+                              : launch_b<0, 1, 0, false>(surfs, list, count, cs);
+    return fovea ? launch_b<0, 2, 0, true>(surfs, list, count, cs) : launch_b<0, 2, 0, false>(surfs, list, count, cs);
+}
 
 // Levels 2 and 1 of the listed strip tiles, LL_2 from the planes written by
 // the coarse pass (streams of three or more levels).

@@ -185,6 +185,7 @@ struct SurfaceJob {
     uint32_t *stamp;   // tile stamps (total_tiles), then coarse stamps (total_ctiles)
     uint8_t *fmask;    // foveation cell bits (foveated surfaces), else null
     int cls;           // decode class (see kClasses)
+    int strip;         // fine tiles are strips (fine: strip-pass arguments), decoded by k_strip_batch
 };
 
 // Decode classes of a batch: one persistent tile-decode launch per wavelet,
@@ -198,6 +199,7 @@ constexpr int kClasses = 6 * kMaxBands;
 struct BatchLists {
     uint2 *coarse[kClasses];
     uint2 *fine[kClasses];
+    uint2 *strip[kClasses];   // strip tiles of the class's strip surfaces
 };
 
 struct RequestJob {
@@ -209,8 +211,9 @@ struct RequestJob {
 };
 
 // Batch counters: decode class c uses [4c] next work item, [4c + 1] coarse
-// items, [4c + 2] fine items; surface s uses [kBatchCtr + 2s] coarse tiles
-// listed and [kBatchCtr + 2s + 1] coarse tiles finished.
+// items, [4c + 2] fine items, [4c + 3] strip items; surface s uses
+// [kBatchCtr + 2s] coarse tiles listed and [kBatchCtr + 2s + 1] coarse
+// tiles finished.
 constexpr int kBatchCtr = 4 * kClasses;
 
 struct StreamHeader {
@@ -276,6 +279,12 @@ cudaError_t launch_decode_strips(const Geom &g, const int16_t *payload, const in
                                  uint8_t *const *out_u8, float *out_f32, int f32_plane,
                                  const uint32_t *tiles, int *counters, int *err, cudaStream_t cs,
                                  bool chroma_pairs = false);
+// Batched strip fine pass: the strip tiles (list of (surface, entry)) of the
+// decode targets of one class whose coarse tiles are done; classes with up
+// to two coefficient frames, 9/7 codes held as 2q + sign(q) or 5/3.
+bool strip_batch_supported(int wavelet, int nb, bool dz_t);
+cudaError_t launch_decode_strips_batch(int wavelet, int nb, bool fovea, bool dz_t, const SurfaceJob *surfs,
+                                       const uint2 *list, const int *count, cudaStream_t cs);
 cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int32_t *table,
                                const Bands &bands, const float *const *ll2, const int *ll2_pitch,
                                uint8_t *const *out_u8, float *out_f32, int f32_plane,

@@ -162,6 +162,7 @@ def _lib():
             "wv_batch_set_timing": (c_int, [vp, c_int]),
             "wv_batch_set_sharing": (c_int, [vp, c_int]),
             "wv_batch_set_wait_limit": (c_int, [vp, c_int]),
+            "wv_batch_set_strips": (c_int, [vp, c_int]),
             "wv_debug_fail_device_allocs": (None, [c_int]),
             "wv_batch_set_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
             "wv_batch_tile_shape": (c_int, [vp, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
@@ -201,7 +202,7 @@ def exported_symbols() -> list[str]:
             "wv_batch_device_bytes", "wv_batch_sync_status", "wv_batch_stats", "wv_batch_set_timing",
             "wv_batch_set_sharing", "wv_batch_set_wait_limit", "wv_debug_fail_device_allocs",
             "wv_batch_set_tile_shape", "wv_batch_tile_shape", "wv_batch_autotune", "wv_batch_completion_ms",
-            "wv_batch_set_memory_limit"]
+            "wv_batch_set_memory_limit", "wv_batch_set_strips"]
 
 
 def _check(rc: int, what: str):
@@ -444,6 +445,10 @@ class Batch:
 
     def set_timing(self, on: bool) -> None:
         _check(_lib().wv_batch_set_timing(self._h, 1 if on else 0), "wv_batch_set_timing")
+
+    def set_strips(self, on: bool) -> None:
+        """Strip fine pass for the targets it takes (default), or square tiles for all."""
+        _check(_lib().wv_batch_set_strips(self._h, 1 if on else 0), "wv_batch_set_strips")
 
     def set_sharing(self, on: bool) -> None:
         _check(_lib().wv_batch_set_sharing(self._h, 1 if on else 0), "wv_batch_set_sharing")

@@ -240,6 +240,32 @@ FOVEA_POSES = [(0.3, 0.1, math.radians(100), 0.35, 0.7), (2.8, -0.4, math.radian
 
 
 @pytest.mark.parametrize("name", ["fov97", "fov53"])
+def test_strip_targets_equal_square_targets(name):
+    """The batched strip fine pass (foveated and not, edge strips as halves)
+    gives the same viewports as square tiles for every target."""
+    from paper_2208_10859_gb300 import wv
+    _, p, _, _ = H.case(name)
+    s = _streams(name)[name]
+    outs = {}
+    for strips in (True, False):
+        b = wv.Batch()
+        b.set_strips(strips)
+        reqs = []
+        for k, (yaw, pitch, fov, r1, r2) in enumerate(FOVEA_POSES):
+            gx, gy = _gaze_with_margin(p, yaw, pitch, r1, r2)
+            for fovea in (True, False):
+                out = torch.zeros((96, 128, 4), dtype=torch.uint8, device="cuda")
+                reqs.append(wv.ViewRequest(s, k % p.num_frames, yaw, pitch, fov, out, fovea, gx, gy, r1, r2))
+        b.decode(reqs)
+        torch.cuda.synchronize()
+        assert b.sync_status() == 0
+        outs[strips] = [r.out.cpu().numpy() for r in reqs]
+        b.close()
+    for a, c in zip(outs[True], outs[False]):
+        np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("name", ["fov97", "fov53"])
 def test_foveated_matches_oracle(name):
     """Foveated requests against the oracle's foveated decode (coefficients of
     levels 1 and 2 outside the kept cells set to zero, then the plain

@@ -37,6 +37,7 @@ def test_bounded_wait_gives_up_and_reports_timeout():
     outs = [torch.zeros((48, 48, 4), dtype=torch.uint8, device="cuda") for _ in range(3)]
     reqs, poses = _requests(s, 3, outs)
     b = wv.Batch()
+    b.set_strips(False)   # square fine tiles: they wait for their target's coarse tiles in the same launch
     b.set_wait_limit(0)
     b.decode(reqs)
     torch.cuda.synchronize()
