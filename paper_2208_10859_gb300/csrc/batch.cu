@@ -67,6 +67,7 @@ struct Surface {
     Geom g;
     int cls;
     bool strip;     // fine tiles are strips (k_strip_batch), else square tiles
+    bool pair;      // reconstruction chroma held as alternating Cb, Cr groups of 4
     int wave;
     size_t bytes;   // device bytes of its stamps, list entries and planes
     size_t recon[3], ll2[3], fmask, stamp;   // arena offsets (inside the wave region)
@@ -283,6 +284,9 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
                 S.recon[p] = o;
                 if (p < S.g.planes) o = align256(o + (size_t)S.g.p[p].w * S.g.p[p].h);
             }
+            // chroma as alternating Cb, Cr groups of 4: strip targets whose
+            // two chroma planes are back to back
+            S.pair = S.strip && S.g.planes == 3 && S.recon[2] == S.recon[1] + (size_t)S.g.p[1].w * S.g.p[1].h;
             for (int p = 0; p < 3; ++p) {
                 S.ll2[p] = o;
                 if (p < S.g.planes && S.g.levels >= 3)
@@ -354,6 +358,10 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         J.fmask = S.foveated ? (uint8_t *)(base + S.fmask) : nullptr;
         J.cls = S.cls;
         J.strip = S.strip ? 1 : 0;
+        if (S.pair) {   // chroma as alternating Cb, Cr groups of 4 (chroma planes adjacent)
+            J.fine.out_pair = 1;
+            J.fine.out_u8[2] = J.fine.out_u8[1] + 4;
+        }
         // the class's tile decode takes only the coarse tiles of strip surfaces
         int need = S.strip ? 0 : (J.fine.a_floats + J.fine.p_floats) * 4;
         if (S.g.levels >= 3) need = std::max(need, (J.coarse.a_floats + J.coarse.p_floats) * 4);
@@ -386,6 +394,7 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         }
         R.rs.planes = S.g.planes;
         R.rs.c420 = S.g.c420;
+        R.rs.c_pair = S.pair ? 1 : 0;
         R.rs.uv = nullptr;
         R.rs.out = (uint8_t *)r.out.dptr;
         R.rs.pitch = r.out.pitch_bytes;
