@@ -15,7 +15,7 @@
 // registers with one warp shuffle per step for the neighbouring lane's edge
 // value; vertical lifting is a running state per column in registers, so a
 // pair of input rows completes a pair of output rows a fixed number of rows
-// above it.  The two LL_1 rows completed this way pass through a four-row
+// above it.  The two LL_1 rows completed this way pass through an eight-row
 // ring in shared memory to the level-1 lanes, which synthesise two pairs of
 // level-1 rows (LL_1 | HL_1, LH_1 | HH_1) in the same way and store four
 // output rows.  No tile-sized array is kept anywhere.
@@ -25,6 +25,13 @@
 // level-2 lanes 1..30 deliver LL_1 columns X0/2 - 4 .. X0/2 + 115 and level-1
 // lanes 1..28 write the strip's 224 columns.  Vertically the first pairs
 // of a tile only warm the running state up (four pairs per level for 9/7).
+//
+// A strip touching the plane's left or right side (an edge strip) may be
+// listed as two half strips of th / 2 rows each: its reflected columns make
+// it the slowest tile, and the launch lasts as long as its slowest tile.
+// The same strips of many decode targets run in one batched launch
+// (k_strip_batch), with foveation (Sec. 3.7) dropping the detail rows of
+// the cells outside its radii in the gather.
 //
 // Symmetric extension (whole-sample, in the interleaved line of every level,
 // as the transform defines it): a source row or column outside the subband
