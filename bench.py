@@ -166,18 +166,28 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def source_digest(path):
+    """SHA-1 of a CUDA source with its // comments and blank lines removed,
+    so that a record stays tied to the code, not to its comments."""
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha1("\n".join(lines).encode()).hexdigest()
+
+
 def traffic_record(name="k_strip_traffic.json", source="strip.cu"):
     """DRAM traffic of a kernel from the committed ncu summary (as a ratio to
     the captured launch's algorithmic bytes), if it was taken on the current
-    kernel source; else None."""
+    kernel code (comments aside); else None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_2208_10859_gb300", "csrc", source), "rb").read()
-    if rec.get("source_sha1") != hashlib.sha1(src).hexdigest():
+    if rec.get("source_digest") != source_digest(os.path.join(ROOT, "paper_2208_10859_gb300", "csrc", source)):
         return None
     return rec
 
