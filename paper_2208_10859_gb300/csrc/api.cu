@@ -111,7 +111,7 @@ int stream_geoms(const wv_stream_desc &d, uint64_t n_payload, Geom *g, Geom *gsq
 
 struct Layout {
     size_t payload, table, recon[3], ll2[3], mask, tiles, ctiles, tile_gen, ctile_gen, counters, err;
-    size_t ll2_1[3], tiles1, ctiles1, counters1, total;   // the second per-viewport set
+    size_t ll2_1[3], tiles1, ctiles1, counters1, recon1[3], total;   // the second per-viewport set
 };
 
 // Device layout of a stream; tile lists and stamps hold the larger tile count
@@ -161,6 +161,10 @@ Layout layout(const Geom &g0, const Geom &gsq, uint64_t n_payload) {
     o = align256(o + (size_t)(g.total_ctiles > 0 ? g.total_ctiles : 1) * 4);
     L.counters1 = o;
     o = align256(o + 64);
+    for (int p = 0; p < 3; ++p) {
+        L.recon1[p] = o;
+        if (p < g.planes) o = align256(o + (size_t)g.p[p].w * g.p[p].h);
+    }
     L.total = o;
     return L;
 }
@@ -207,7 +211,9 @@ cudaError_t launch_fine(wv_stream *s, const Bands &b, const float *const *ll2, u
     const Geom &g = active_geom(s);
     if (strip_mode(s)) {
         // into the stream's reconstruction planes: chroma in alternating Cb, Cr groups
-        const bool pairs = out_u8[1] == s->recon[1] && out_u8[2] == s->recon[2] && recon_pairs(s);
+        const bool own = (out_u8[1] == s->recon[1] && out_u8[2] == s->recon[2]) ||
+                         (out_u8[1] == s->recon1[1] && out_u8[2] == s->recon1[2]);
+        const bool pairs = own && recon_pairs(s);
         uint8_t *const outs[3] = {out_u8[0], out_u8[1], pairs ? out_u8[1] + 4 : out_u8[2]};
         return launch_decode_strips(g, s->payload, s->table, b, ll2, s->ll2_pitch, outs, f32, f32_plane, tiles,
                                     counters, s->err, cs, pairs);
@@ -261,8 +267,10 @@ cudaError_t ensure_aux(wv_stream *s) {
     int lo = 0, hi = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaEventCreateWithFlags(&s->ev_ready[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fine[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_free[k], cudaEventDisableTiming);
     }
     return e;
@@ -288,8 +296,13 @@ void mark_sets_used(wv_stream *s) {
     cudaEventRecord(s->ev_free[1], s->cs);
 }
 
-// Overlapped viewport decode: footprint, selection and coarse pass on aux
-// into buffer set k (after cs has finished with set k), fine pass on cs.
+// Overlapped viewport decode into buffer set k, three stages on three
+// streams: footprint, selection and coarse pass on aux (once the fine pass
+// of two viewports ago and every cs use of set k are done), the fine pass
+// into set k's reconstruction on fs (once the coarse pass is done and the
+// resampling of two viewports ago has read that reconstruction), and cs
+// waits for the fine pass; the caller's resampling then runs on cs while
+// the next viewport's fine pass writes the other set.
 int decode_region_overlapped(wv_stream *s, const View &v, const Bands &b, uint32_t gen) {
     const Geom &g = active_geom(s);
     const int k = s->slot;
@@ -297,16 +310,22 @@ int decode_region_overlapped(wv_stream *s, const View &v, const Bands &b, uint32
     uint32_t *tiles = k ? s->tiles1 : s->tiles, *ctiles = k ? s->ctiles1 : s->ctiles;
     int *counters = k ? s->counters1 : s->counters;
     float *ll2[3] = {k ? s->ll2_1[0] : s->ll2[0], k ? s->ll2_1[1] : s->ll2[1], k ? s->ll2_1[2] : s->ll2[2]};
-    cudaError_t e = cudaStreamWaitEvent(s->aux, s->ev_free[k], 0);
+    uint8_t *const *recon = k ? s->recon1 : s->recon;
+    cudaError_t e = cudaStreamWaitEvent(s->aux, s->ev_fine[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_free[k], 0);
     if (e != cudaSuccess) return WV_ERR_CUDA;
     launch_footprint(g, v, s->mask, s->tile_gen, s->ctile_gen, gen, counters, s->aux);
     launch_select_tiles(g, s->tile_gen, s->ctile_gen, gen, tiles, ctiles, counters, s->aux);
     e = launch_decode_coarse(g, s->payload, s->table, b, ll2, s->ll2_pitch, ctiles, counters + 1, s->err, s->aux);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[k], s->aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_ready[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->fs, s->ev_ready[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->fs, s->ev_free[k], 0);
     const float *ll2c[3] = {ll2[0], ll2[1], ll2[2]};
-    if (e == cudaSuccess) e = launch_fine(s, b, ll2c, s->recon, nullptr, -1, tiles, counters, s->cs);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev_free[k], s->cs);
+    if (e == cudaSuccess) e = launch_fine(s, b, ll2c, recon, nullptr, -1, tiles, counters, s->fs);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_fine[k], s->fs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_fine[k], 0);
+    s->cur = k;
+    s->pending = true;
     return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
 }
 
@@ -328,7 +347,17 @@ int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, in
     prof_end(s);
     const cudaError_t e = run_decode(s, b, s->recon, nullptr, -1);
     mark_sets_used(s);
+    s->cur = 0;
+    s->pending = true;
     return e == cudaSuccess ? WV_OK : WV_ERR_CUDA;
+}
+
+uint8_t *const *recon_planes(const wv_stream *s) { return s->cur ? s->recon1 : s->recon; }
+
+void release_recon(wv_stream *s) {
+    if (!s->pending) return;
+    s->pending = false;
+    if (s->aux && s->overlap) cudaEventRecord(s->ev_free[s->cur], s->cs);
 }
 
 }  // namespace wv
@@ -348,9 +377,10 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     if (rc != WV_OK) return rc;
     const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, rows, row0);
     prof_begin(s, kKResample);
-    launch_resample(g, v, s->recon, nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr, nullptr,
-                    nullptr, recon_pairs(s));
+    launch_resample(g, v, recon_planes(s), nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr,
+                    nullptr, nullptr, recon_pairs(s));
     prof_end(s);
+    release_recon(s);
     return cuda_err(cudaGetLastError());
 }
 
@@ -793,7 +823,9 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
     if (!host_payload) s->payload = (int16_t *)(base + L.payload);
     s->table = (int32_t *)(base + L.table);
     for (int p = 0; p < 3; ++p) s->recon[p] = p < s->g.planes ? (uint8_t *)(base + L.recon[p]) : nullptr;
-    s->pair_ok = s->g.planes == 3 && L.recon[2] == L.recon[1] + (size_t)s->g.p[1].w * s->g.p[1].h;
+    for (int p = 0; p < 3; ++p) s->recon1[p] = p < s->g.planes ? (uint8_t *)(base + L.recon1[p]) : nullptr;
+    s->pair_ok = s->g.planes == 3 && L.recon[2] == L.recon[1] + (size_t)s->g.p[1].w * s->g.p[1].h &&
+                 L.recon1[2] == L.recon1[1] + (size_t)s->g.p[1].w * s->g.p[1].h;
     s->mask = (uint8_t *)(base + L.mask);
     s->tiles = (uint32_t *)(base + L.tiles);
     s->ctiles = (uint32_t *)(base + L.ctiles);
@@ -843,6 +875,7 @@ int wv_open_stream_ex(const void *bytes, size_t n, void *device_mem, size_t devi
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon[0], 0, L.tiles - L.recon[0], s->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.recon1[0], 0, L.total - L.recon1[0], s->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.tile_gen, 0, L.err + 64 - L.tile_gen, s->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + L.ll2_1[0], 0, L.total - L.ll2_1[0], s->cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
@@ -870,6 +903,12 @@ void wv_close_stream(wv_stream *s) {
         cudaStreamSynchronize(s->aux);
         cudaStreamDestroy(s->aux);
     }
+    if (s->fs) {
+        cudaStreamSynchronize(s->fs);
+        cudaStreamDestroy(s->fs);
+    }
+    for (cudaEvent_t e : {s->ev_fine[0], s->ev_fine[1]})
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {s->ev_ready[0], s->ev_ready[1], s->ev_free[0], s->ev_free[1]})
         if (e) cudaEventDestroy(e);
     if (s->host_payload) cudaFreeHost(s->host_payload);
@@ -911,6 +950,10 @@ int wv_decode_full(wv_stream *s, int frame, int plane, void *dptr, int as_float)
     if (split_mode(s)) launch_all_ctiles(g, plane, s->ctiles, s->counters, s->cs);
     cudaError_t e = run_decode(s, stream_bands(s, frame), outs, f32, as_float ? plane : -1);
     mark_sets_used(s);
+    if (!dptr) {   // set 0's reconstruction now holds the decode (for wv_resample_at)
+        s->cur = 0;
+        s->pending = true;
+    }
     if (e != cudaSuccess) return WV_ERR_CUDA;
     return cuda_err(cudaGetLastError());
 }
@@ -960,8 +1003,9 @@ int wv_debug_project(wv_stream *s, float yaw, float pitch, float fov, int out_w,
 int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
     if (!s || !uv_dev || check_image(out) != WV_OK) return WV_ERR_ARG;
     View v = make_view(0.f, 0.f, 1.f, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
-    launch_resample(s->g, v, s->recon, uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr, nullptr,
-                    nullptr, recon_pairs(s));
+    launch_resample(s->g, v, recon_planes(s), uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr,
+                    nullptr, nullptr, recon_pairs(s));
+    release_recon(s);
     return cuda_err(cudaGetLastError());
 }
 

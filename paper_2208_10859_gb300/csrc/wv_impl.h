@@ -324,6 +324,10 @@ cudaError_t opt_in_smem(const void *fn, int bytes);
 // and Cr groups of 4 samples: the strip fine pass writes them so (decode
 // mode 0), the square-tile passes plane by plane.
 bool recon_pairs(const wv_stream *s);
+// The reconstruction planes of the stream's last decode, and the release of
+// its set once the resampling that reads them is enqueued on cs.
+uint8_t *const *recon_planes(const wv_stream *s);
+void release_recon(wv_stream *s);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);
@@ -369,13 +373,21 @@ struct wv_stream {
     // footprint, selection and coarse pass of a viewport (on the internal
     // stream `aux`) run while the previous viewport's fine pass and
     // resampling (on cs) are still executing.  Set 0 is the fields above.
+    // The sets also hold a reconstruction each: a viewport's fine pass (on
+    // the internal stream `fs`) writes one while the previous viewport's
+    // resampling (on cs) reads the other.
     uint32_t *tiles1 = nullptr, *ctiles1 = nullptr;
     int *counters1 = nullptr;
     float *ll2_1[3] = {nullptr, nullptr, nullptr};
+    uint8_t *recon1[3] = {nullptr, nullptr, nullptr};
     int slot = 0;
+    int cur = 0;             // the set whose reconstruction holds the last decode
+    bool pending = false;    // the last decode's set is released after its resampling on cs
     bool overlap = true;
     cudaStream_t aux = nullptr;
+    cudaStream_t fs = nullptr;
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // set k's coarse pass done (aux)
+    cudaEvent_t ev_fine[2] = {nullptr, nullptr};    // set k's fine pass done (fs)
     cudaEvent_t ev_free[2] = {nullptr, nullptr};    // cs no longer reads set k
     uint64_t n_payload = 0;
     void *host_payload = nullptr;   // WV_OPEN_HOST_PAYLOAD: pinned, mapped coefficient store
