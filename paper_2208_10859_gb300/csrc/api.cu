@@ -354,8 +354,8 @@ int decode_region(wv_stream *s, int frame, float yaw, float pitch, float fov, in
 
 uint8_t *const *recon_planes(const wv_stream *s) { return s->cur ? s->recon1 : s->recon; }
 
-void release_recon(wv_stream *s) {
-    if (!s->pending) return;
+void release_recon(wv_stream *s, bool again) {
+    if (!s->pending && !again) return;
     s->pending = false;
     if (s->aux && s->overlap) cudaEventRecord(s->ev_free[s->cur], s->cs);
 }
@@ -1005,7 +1005,7 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
     View v = make_view(0.f, 0.f, 1.f, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
     launch_resample(s->g, v, recon_planes(s), uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr,
                     nullptr, nullptr, recon_pairs(s));
-    release_recon(s);
+    release_recon(s, true);   // any number of reads of the last decode: each releases its set again
     return cuda_err(cudaGetLastError());
 }
 

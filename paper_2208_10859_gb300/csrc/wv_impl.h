@@ -327,7 +327,7 @@ bool recon_pairs(const wv_stream *s);
 // The reconstruction planes of the stream's last decode, and the release of
 // its set once the resampling that reads them is enqueued on cs.
 uint8_t *const *recon_planes(const wv_stream *s);
-void release_recon(wv_stream *s);
+void release_recon(wv_stream *s, bool again = false);
 void launch_resample_batch(const RequestJob *reqs, int n, int max_w, int max_h, cudaStream_t cs);
 size_t batch_held_bytes(const wv_batch *b);   // device bytes a batch context holds (no sync)
 void launch_project(const View &v, float *uv, cudaStream_t cs);
