@@ -167,12 +167,20 @@ def measured_peak_hbm():
 
 
 def source_digest(path):
-    """SHA-1 of a CUDA source with its // comments and blank lines removed,
-    so that a record stays tied to the code, not to its comments."""
-    lines = []
+    """SHA-1 of a CUDA source as the normal build compiles it: // comments,
+    blank lines and the `#if WV_CHECKED` branches (the bounds-check build)
+    removed, so that a record stays tied to the code it was taken on."""
+    lines, state = [], 0   # 0 plain code, 1 inside #if WV_CHECKED, 2 inside its #else
     for line in open(path, encoding="utf-8"):
         code = line.split("//", 1)[0].rstrip()
-        if code:
+        d = code.strip()
+        if d == "#if WV_CHECKED":
+            state = 1
+        elif d == "#else" and state == 1:
+            state = 2
+        elif d == "#endif" and state:
+            state = 0
+        elif state != 1 and code:
             lines.append(code)
     return hashlib.sha1("\n".join(lines).encode()).hexdigest()
 

@@ -104,7 +104,12 @@ int parse(const void *bytes, size_t n, wv_stream_desc *d, StreamHeader *h) {
 int stream_geoms(const wv_stream_desc &d, uint64_t n_payload, Geom *g, Geom *gsq) {
     const int rc = build_geom(d, gsq);
     if (rc != WV_OK) return rc;
-    if (strip_eligible(d, n_payload)) return build_geom_strip(d, g);
+    gsq->n_blocks = (int)std::min<uint64_t>(n_payload, 0x7fffffff);
+    if (strip_eligible(d, n_payload)) {
+        const int rs = build_geom_strip(d, g);
+        g->n_blocks = gsq->n_blocks;
+        return rs;
+    }
     *g = *gsq;
     return WV_OK;
 }
@@ -378,7 +383,7 @@ int decode_viewport(wv_stream *s, int frame, float yaw, float pitch, float fov,
     const View v = make_view(yaw, pitch, fov, out->width, out->height, g.p[0].w, rows, row0);
     prof_begin(s, kKResample);
     launch_resample(g, v, recon_planes(s), nullptr, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr,
-                    nullptr, nullptr, recon_pairs(s));
+                    nullptr, nullptr, recon_pairs(s), s->err);
     prof_end(s);
     release_recon(s);
     return cuda_err(cudaGetLastError());
@@ -1004,7 +1009,7 @@ int wv_resample_at(wv_stream *s, const float *uv_dev, const wv_image *out) {
     if (!s || !uv_dev || check_image(out) != WV_OK) return WV_ERR_ARG;
     View v = make_view(0.f, 0.f, 1.f, out->width, out->height, s->g.p[0].w, s->g.p[0].h);
     launch_resample(s->g, v, recon_planes(s), uv_dev, (uint8_t *)out->dptr, out->pitch_bytes, s->cs, nullptr,
-                    nullptr, nullptr, recon_pairs(s));
+                    nullptr, nullptr, recon_pairs(s), s->err);
     release_recon(s, true);   // any number of reads of the last decode: each releases its set again
     return cuda_err(cudaGetLastError());
 }

@@ -200,6 +200,7 @@ int plan_batch(const wv_batch *b, const wv_request *reqs, int n, Plan &P) {
                                : build_geom_rect(r.s->desc, &S.g, ts.tw, ts.th, ts.ctile);
         if (gr != WV_OK) return WV_ERR_ARG;
         S.g.dz_t = sg.dz_t;   // the code form of the stream's device payload
+        S.g.n_blocks = sg.n_blocks;
         // 1 + tlevels coefficient frames
         const int group = S.g.dz_t ? 4 + (S.foveated ? 1 : 0) : 2 * S.g.wavelet + (S.foveated ? 1 : 0);
         S.cls = kMaxBands * group + S.g.tlevels;
@@ -315,6 +316,7 @@ TileArgs pass_args(const Surface &S, char *base, int *err, bool coarse) {
     a.err = err;
     a.f32_plane = -1;
     a.fmask = S.foveated ? (const uint8_t *)(base + S.fmask) : nullptr;
+    if (kChecked) a.n_slots = S.g.n_blocks;
     const bool split = S.g.levels >= 3;
     if (coarse) {
         a.l_top = S.g.levels;
@@ -395,6 +397,7 @@ void fill_jobs(wv_batch *b, const wv_request *reqs, int n, Plan &P) {
         R.rs.planes = S.g.planes;
         R.rs.c420 = S.g.c420;
         R.rs.c_pair = S.pair ? 1 : 0;
+        R.rs.err = err;
         R.rs.uv = nullptr;
         R.rs.out = (uint8_t *)r.out.dptr;
         R.rs.pitch = r.out.pitch_bytes;

@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             reinterpret_cast<int *>(&sa)[k] = __ldg(src + k);
         __syncthreads();
         float *P = smem + sa.a_floats;   // a_floats and p_floats fit the launch's shared memory
-        decode_one<WAV, NB, FOV, QM>(sa, w.y, A, P);
+        decode_one<WAV, NB, FOV, QM, kChecked>(sa, w.y, A, P);
         if (kind == 0) __threadfence();   // LL_2 stores visible GPU-wide before the count
         __syncthreads();
         if (kind == 0 && threadIdx.x == 0) atomicAdd(&surf[2 * (int)w.x + 1], 1);
@@ -925,7 +925,7 @@ void fill_tile_scales(TileArgs &a) {
 
 namespace {
 
-template <int WAV, int NB, int QM = 0, bool CHK = false>
+template <int WAV, int NB, int QM = 0, bool CHK = kChecked>
 cudaError_t launch_t(const TileArgs &a, int grid, int threads, cudaStream_t cs) {
     const int smem = (a.a_floats + a.p_floats) * 4;
     cudaError_t e = opt_in_smem(reinterpret_cast<const void *>(k_tiles<WAV, NB, QM, CHK>), smem);
@@ -958,7 +958,9 @@ cudaError_t launch_args(TileArgs &a, cudaStream_t cs) {
     const int threads = coarse ? kThreads / 2 : kThreads;
     const int grid = decode_tiles_grid(a.g) * (coarse ? 2 : 1);
     const int nb = a.bands.n;
-    if (a.n_slots > 0) {   // table entries checked against the payload's block count (q codes only)
+    const bool table_check = a.n_slots > 0;
+    if (kChecked && !table_check) a.n_slots = a.g.n_blocks;   // every variant checks in WV_CHECKED builds
+    if (table_check) {   // table entries checked against the payload's block count (q codes only)
         if (a.g.quant != 0 || a.g.dz_t) return cudaErrorInvalidValue;
         if (a.g.wavelet == WV_WAVELET_97) {
             switch (nb) {

@@ -917,7 +917,8 @@ int wv_decode_viewport_filtered(wv_stream *s, int frame, float yaw, float pitch,
     int row0, rows;
     eye_view(s->g, 0, &row0, &rows);   // eye 0 (the top half of a stereo frame)
     const View v = make_view(yaw, pitch, fov, out->width, out->height, s->g.p[0].w, rows, row0);
-    launch_resample(s->g, v, recon_planes(s), nullptr, nullptr, 0, s->cs, c->xbuf, c->cb, c->cr, recon_pairs(s));
+    launch_resample(s->g, v, recon_planes(s), nullptr, nullptr, 0, s->cs, c->xbuf, c->cb, c->cr, recon_pairs(s),
+                    s->err);
     release_recon(s);
     ConvArgs fin;
     memset(&fin, 0, sizeof(fin));

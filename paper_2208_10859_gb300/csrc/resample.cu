@@ -103,9 +103,17 @@ __device__ __forceinline__ void blend_pair(const uint8_t *__restrict__ img, cons
 
 // Y, Cb, Cr of luma position (u, v); Cb and Cr share their taps.  Rows
 // clamp to the eye's part of the frame (all of it for mono streams).
+// WV_CHECKED builds: every tap offset inside the w x h plane.
+__device__ __forceinline__ bool taps_in(const Taps &t, int w, int h, int *err) {
+    const long long n = (long long)w * h;
+    return checked_in(t.a0, n, err) && checked_in(t.a1, n, err) && checked_in(t.b0, n, err) &&
+           checked_in(t.b1, n, err);
+}
+
 __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, float v, int &y, int &cb,
                                              int &cr) {
-    y = blend(a.plane[0], bilinear_taps(a.w[0], a.v.row0, a.v.rows, u, v));
+    const Taps ty = bilinear_taps(a.w[0], a.v.row0, a.v.rows, u, v);
+    y = !kChecked || taps_in(ty, a.w[0], a.h[0], a.err) ? blend(a.plane[0], ty) : 0;
     cb = cr = 128;
     if (a.planes == 3) {
         float uc = u, vc = v;
@@ -115,6 +123,7 @@ __device__ __forceinline__ void sample_ycbcr(const ResampleArgs &a, float u, flo
         }
         const int sh = a.c420 ? 1 : 0;
         const Taps t = bilinear_taps(a.w[1], a.v.row0 >> sh, a.v.rows >> sh, uc, vc);
+        if (kChecked && !taps_in(t, a.w[1], a.h[1], a.err)) return;
         if (a.c_pair) {
             blend_pair(a.plane[1], t, cb, cr);
         } else {
@@ -203,9 +212,10 @@ __global__ void k_resample_batch(const RequestJob *__restrict__ reqs) {
 
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane,
-                     uint8_t *cb_plane, uint8_t *cr_plane, bool c_pair) {
+                     uint8_t *cb_plane, uint8_t *cr_plane, bool c_pair, int *err) {
     ResampleArgs a;
     memset(&a, 0, sizeof(a));
+    a.err = err;
     a.y_plane = y_plane;
     a.cb_plane = cb_plane;
     a.cr_plane = cr_plane;

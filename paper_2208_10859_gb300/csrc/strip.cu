@@ -172,7 +172,12 @@ __device__ __forceinline__ void sub_refresh(const TileArgs &a, const PlaneGeom &
     const int bid = pg.base[level][sub] + by * pg.nbx[level] + (lc.kx >> g.log2b);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
+#if WV_CHECKED
+        int slot = lc.fast ? __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]) : -1;
+        if (slot >= 0 && !checked_in(slot, g.n_blocks, a.err)) slot = -1;
+#else
         const int slot = lc.fast ? __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]) : -1;
+#endif
         r.off[b] = slot >= 0 ? ((uint32_t)slot << (2 * g.log2b)) + (uint32_t)(lc.kx & (g.block - 1)) : kNone;
     }
 }
@@ -188,7 +193,12 @@ __device__ __noinline__ void code1(const TileArgs &a, const PlaneGeom &pg, int l
     const size_t off = (size_t)((ky & bm) << lb) + (kx & bm);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
+#if WV_CHECKED
+        int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+        if (slot >= 0 && !checked_in(slot, g.n_blocks, a.err)) slot = -1;
+#else
         const int slot = __ldg(&a.table[(size_t)a.bands.t[b] * g.nbpf + bid]);
+#endif
         v[b] = slot >= 0 ? (uint32_t)(uint16_t)__ldg(&a.payload[((size_t)slot << (2 * lb)) + off]) : 0u;
     }
 }
@@ -576,7 +586,14 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
         if (t < P2) {
             const int sig = (Y0 >> 1) - 6 + 2 * t;
             const int ke = refl(sig, H2) >> 1, ko = refl(sig + 1, H2) >> 1;
+#if WV_CHECKED
+            const bool ll_ok =
+                !l2.fast || checked_in((long long)ke * llpitch + l2.kx + 1, (long long)llpitch * (H >> 2), a.err);
+            cp_async(St::ll(sb, lane), l2.fast && ll_ok ? llp + (size_t)ke * llpitch + l2.kx : llp, 8,
+                     l2.fast && ll_ok);
+#else
             cp_async(St::ll(sb, lane), l2.fast ? llp + (size_t)ke * llpitch + l2.kx : llp, 8, l2.fast);
+#endif
             const bool ke2 = !FOV || !l2.fast || fov_keep(a, pg, 2, l2.kx, ke);
             const bool ko2 = !FOV || !l2.fast || fov_keep(a, pg, 2, l2.kx, ko);
             sub_issue<NB, 1>(a, pg, 2, 1, ke, l2, r2[1], [&](int b) { return St::l2(sb, 1, b, lane); }, ke2);
@@ -623,7 +640,15 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                 } else {
 #pragma unroll
                     for (int m = 0; m < 2; ++m)
+#if WV_CHECKED
+                    {
+                        const long long li = (long long)ke * llpitch + (refl(l2.c0 + 2 * m, W2) >> 1);
+                        ll[m] = checked_in(li, (long long)llpitch * (H >> 2), a.err) ? from_f<T>(__ldcg(llp + li))
+                                                                                      : T(0);
+                    }
+#else
                         ll[m] = from_f<T>(__ldcg(llp + (size_t)ke * llpitch + (refl(l2.c0 + 2 * m, W2) >> 1)));
+#endif
                 }
                 sub_fetch<NB, 1, FOV>(a, pg, 2, 1, 1, W2, ke, l2, [&](int b) { return St::l2(sb, 1, b, lane); }, w);
                 dq_row<WAV, NB, QM, 1>(a, w, a.scale[2][1], hl);
@@ -731,6 +756,9 @@ __device__ __forceinline__ void strip_tile(const TileArgs &a, uint32_t e, float 
                         }
                         // two groups of 4 samples: adjacent, or (chroma groups)
                         // with the other chroma plane's group between them
+#if WV_CHECKED
+                        if (!checked_in((long long)o + 7, (long long)W * H, a.err)) continue;
+#endif
                         uint32_t *d = reinterpret_cast<uint32_t *>(out8 + (o << pair_sh));
                         d[0] = pack4_sat(p[0], p[1], p[2], p[3]);
                         d[1 << pair_sh] = pack4_sat(p[4], p[5], p[6], p[7]);

@@ -74,7 +74,19 @@ struct Geom {
     // (tw / 4) tx + wx1, rows (th / 4) ty + wy0 .. (th / 4) ty + wy1 (before
     // symmetric extension); the coarse tiles holding it are decoded first
     int wx0, wx1, wy0, wy1;
+    // payload blocks of the stream (table entries are below it; checked at
+    // open on the host, and on the device in WV_CHECKED builds)
+    int n_blocks;
 };
+
+// WV_CHECKED builds (build(checked=True)): the kernels test the indices
+// their data decide (table entries, output and tap offsets, stamp indices)
+// and on a violation record WV_ERR_DEVICE in the error word and skip the
+// access instead of faulting.
+#ifndef WV_CHECKED
+#define WV_CHECKED 0
+#endif
+constexpr bool kChecked = WV_CHECKED != 0;
 
 // Coefficient frames that rebuild one frame (inverse inter-frame Haar):
 // t[0] is the low band L_k, t[1..] the detail bands from level k down to 1;
@@ -173,6 +185,7 @@ struct ResampleArgs {
     float *y_plane;
     uint8_t *cb_plane, *cr_plane;
     int c_pair;   // plane[1] holds Cb and Cr in alternating 4-sample groups (plane[2] unused)
+    int *err;     // WV_CHECKED builds: error word for out-of-plane taps
 };
 
 // ---- batched decoding ---------------------------------------------------------
@@ -291,7 +304,8 @@ cudaError_t launch_decode_fine(const Geom &g, const int16_t *payload, const int3
                                const uint32_t *tiles, const int *count, int *err, cudaStream_t cs);
 void launch_resample(const Geom &g, const View &v, uint8_t *const *recon, const float *uv,
                      uint8_t *out, size_t pitch, cudaStream_t cs, float *y_plane = nullptr,
-                     uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr, bool c_pair = false);
+                     uint8_t *cb_plane = nullptr, uint8_t *cr_plane = nullptr, bool c_pair = false,
+                     int *err = nullptr);
 void fill_tile_scales(TileArgs &a);
 void smem_needs_cached(int wavelet, int l_top, int l_bot, int tw, int th, int *a_floats, int *p_floats);
 
@@ -493,6 +507,18 @@ __device__ __forceinline__ uchar4 to_rgba(int y, int cb, int cr) {
 
 __device__ __forceinline__ void record_error(int *err, int code) {
     atomicCAS(err, 0, code);
+}
+
+// WV_CHECKED builds: whether 0 <= i < n, recording WV_ERR_DEVICE when not;
+// always true in normal builds (the test compiles away).
+__device__ __forceinline__ bool checked_in(long long i, long long n, int *err) {
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        if (i >= 0 && i < n) return true;
+        if (err) record_error(err, WV_ERR_DEVICE);
+        return false;
+    }
 }
 
 }  // namespace wv

@@ -85,15 +85,17 @@ _LIB = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library the binding loads: libwv.so, or the WV_CHECKED build when
+    the environment variable WV_CHECKED is 1."""
+    return _build.LIB_CHECKED if os.environ.get("WV_CHECKED") == "1" else _build.LIB
 
 
 def _lib():
     global _LIB
     if _LIB is None:
-        path = _build.LIB
+        path = lib_path()
         if not os.path.exists(path):
-            raise ImportError(f"libwv.so is not built ({path}); run __graft_entry__.build()")
+            raise ImportError(f"{os.path.basename(path)} is not built ({path}); run __graft_entry__.build()")
         L = ctypes.CDLL(path)
         c_int, c_size, vp, fl = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_float
         sig = {
