@@ -56,6 +56,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wv_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# host-side sanitizers: with WV_ORACLE_SANITIZE=1 the oracle loads a build
+# of its C core with AddressSanitizer and UndefinedBehaviorSanitizer (the
+# process must preload the ASan runtime)
+_SAN_PATH = os.path.join(_BUILD, "liboracle_san.so")
 _lib = None
 
 WAVELET_53 = 0
@@ -65,6 +69,19 @@ WAVELET_97 = 1
 # --------------------------------------------------------------------------
 # native lifting core
 # --------------------------------------------------------------------------
+
+def build_sanitized() -> str:
+    """Compile wv_oracle.c with AddressSanitizer and UndefinedBehaviorSanitizer
+    (single-threaded) into oracle/_build/liboracle_san.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not os.path.exists(_SAN_PATH) or os.path.getmtime(_SAN_PATH) < os.path.getmtime(_SRC):
+        tmp = _SAN_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O1", "-g", "-fPIC", "-shared", "-std=c99",
+                               "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+                               "-fno-omit-frame-pointer", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SAN_PATH)
+    return _SAN_PATH
+
 
 def build() -> str:
     """Compile wv_oracle.c with gcc into oracle/_build/liboracle.so (with
@@ -91,7 +108,7 @@ def set_threads(n: int) -> int:
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(build_sanitized() if os.environ.get("WV_ORACLE_SANITIZE") == "1" else build())
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int64)
         L = ctypes.c_long
