@@ -21,6 +21,13 @@ LIB = os.path.join(BUILD, "libwv.so")
 # environment variable WV_CHECKED is 1
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(BUILD_CHECKED, "libwv_checked.so")
+# host code under AddressSanitizer and UndefinedBehaviorSanitizer (device
+# code unchanged): loaded when the environment variable WV_SANITIZE is 1,
+# with the sanitizer runtimes preloaded
+BUILD_SAN = os.path.join(HERE, "_build_san")
+LIB_SAN = os.path.join(BUILD_SAN, "libwv_san.so")
+SAN_FLAGS = ["-Xcompiler=-fsanitize=address", "-Xcompiler=-fsanitize=undefined",
+             "-Xcompiler=-fno-sanitize-recover=undefined", "-Xcompiler=-fno-omit-frame-pointer"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -48,15 +55,16 @@ def _stale(lib: str) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
-          checked: bool = False) -> str:
-    """Compile and link libwv.so (checked: libwv_checked.so with WV_CHECKED=1);
-    returns its path."""
-    lib, out_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+          checked: bool = False, sanitize: bool = False) -> str:
+    """Compile and link libwv.so (checked: libwv_checked.so with WV_CHECKED=1;
+    sanitize: libwv_san.so, host code under ASan and UBSan); returns its path."""
+    lib, out_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB_SAN, BUILD_SAN) if sanitize else (LIB, BUILD)
     if not force and not _stale(lib):
         return lib
     os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = ARCH + NVCC_FLAGS + list(extra_flags or []) + (["-DWV_CHECKED=1"] if checked else [])
+    flags = ARCH + NVCC_FLAGS + list(extra_flags or []) + (["-DWV_CHECKED=1"] if checked else []) + \
+        (SAN_FLAGS if sanitize else [])
 
     def compile_one(src: str) -> str:
         obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
@@ -82,4 +90,5 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv,
+                sanitize="--sanitize" in sys.argv))

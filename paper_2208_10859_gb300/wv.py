@@ -85,9 +85,14 @@ _LIB = None
 
 
 def lib_path() -> str:
-    """The library the binding loads: libwv.so, or the WV_CHECKED build when
-    the environment variable WV_CHECKED is 1."""
-    return _build.LIB_CHECKED if os.environ.get("WV_CHECKED") == "1" else _build.LIB
+    """The library the binding loads: libwv.so, the WV_CHECKED build when the
+    environment variable WV_CHECKED is 1, or the host-sanitizer build when
+    WV_SANITIZE is 1."""
+    if os.environ.get("WV_CHECKED") == "1":
+        return _build.LIB_CHECKED
+    if os.environ.get("WV_SANITIZE") == "1":
+        return _build.LIB_SAN
+    return _build.LIB
 
 
 def _lib():
