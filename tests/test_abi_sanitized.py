@@ -58,6 +58,29 @@ for s in streams:
         query(b)
 for n in (16, 128, 1000, 5000):
     query(rng.integers(0, 256, n, dtype=np.uint8).tobytes())
+# stream descriptions of every shape, valid or not: the geometry builder
+scratch, biggest = ctypes.c_size_t(), ctypes.c_size_t()
+ok_desc = 0
+for _ in range(400):
+    d = wv.StreamDesc()
+    d.width, d.height = (int(x) for x in rng.choice([0, 2, 30, 32, 64, 96, 320, 2048, 16384, 16416, -32], 2))
+    d.planes = int(rng.choice([0, 1, 2, 3, 4]))
+    d.chroma_420 = int(rng.integers(-1, 3))
+    d.levels = int(rng.integers(-1, 9))
+    d.wavelet = int(rng.integers(-1, 3))
+    d.num_frames = int(rng.choice([0, 1, 2, 3, 4, 8]))
+    d.tlevels = int(rng.integers(-1, 5))
+    d.block = int(rng.choice([0, 8, 16, 24, 32, 256, 512]))
+    d.quant = int(rng.integers(-1, 3))
+    d.step = float(rng.choice([0.0, 1.0, 2.5, 4.0, -1.0, float("nan")]))
+    d.stereo = int(rng.integers(-1, 3))
+    rc = L.wv_encode_sizes(ctypes.byref(d), ctypes.byref(scratch), ctypes.byref(biggest))
+    assert rc == 0 or -8 < rc < 0, rc
+    ok_desc += rc == 0
+for s in streams[:2]:   # the descriptions of valid streams
+    assert L.wv_stream_query(ctypes.create_string_buffer(s, len(s)), len(s), ctypes.byref(desc), None) == 0
+    assert L.wv_encode_sizes(ctypes.byref(desc), ctypes.byref(scratch), ctypes.byref(biggest)) == 0
+    assert biggest.value > 0
 # argument checks and no CUDA device: errors, never a CPU fallback
 assert L.wv_stream_query(None, 0, None, None) < 0
 assert L.wv_decode_viewport(None, 0, 0.0, 0.0, 1.0, None) == -1
